@@ -1,0 +1,161 @@
+"""CPU oracle for permuted FHT-FSCL decoding of Reed-Muller codes (arXiv 2108.12550).
+
+TEST INFRASTRUCTURE ONLY: the reference the GPU decoder is checked against. Only the test
+suite, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg may import this
+package. The decoder product never imports it and shares no code with it.
+
+The arithmetic lives in ``rm_oracle.c`` / ``pfht_core.inc`` (plain C, FP64 and int64 modes,
+following Algorithms 2-5 and Eqs. (2)-(8) of the paper step by step); this module only
+compiles that file with gcc and marshals numpy arrays through ctypes.
+
+Parity status: every function here is pinned by ``tests/test_oracle_pins.py`` against
+closed forms, brute force and the paper's printed FER values. Unpinned: the exact
+complexity count C of the paper (its Table 1 cannot be reproduced, so ``ops`` is this
+oracle's own count).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "librmoracle.so")
+_SOURCES = [os.path.join(_HERE, "rm_oracle.c"), os.path.join(_HERE, "pfht_core.inc")]
+_lib = None
+
+MAXM = 10
+PERM_REC = MAXM + 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (portable flags only: it also builds on the Arm host)."""
+    stale = not os.path.exists(_LIB_PATH) or any(
+        os.path.getmtime(s) > os.path.getmtime(_LIB_PATH) for s in _SOURCES)
+    if force or stale:
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-Wall", "-shared", "-fPIC", "-pthread",
+                               _SOURCES[0], "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.c_void_p
+        i, i64 = ctypes.c_int, ctypes.c_int64
+        for name in ("rmo_decode_f64", "rmo_decode_i64"):
+            getattr(lib, name).argtypes = [i, i, i, i, P, P, i64, i, P, P, P, P, P, P]
+            getattr(lib, name).restype = i
+        for name in ("rmo_aut_ssc_f64", "rmo_aut_ssc_i64"):
+            getattr(lib, name).argtypes = [i, i, i, P, P, i64, i, P, P, P, P]
+            getattr(lib, name).restype = i
+        for name in ("rmo_fhtl_f64", "rmo_spcl_f64"):
+            getattr(lib, name).argtypes = [i, i, P, P, P, P, P]
+            getattr(lib, name).restype = i
+        lib.rmo_fht_f64.argtypes = [P, i]
+        lib.rmo_fht_f64.restype = None
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _k(m, r):
+    return sum(1 for i in range(1 << m) if bin(i).count("1") >= m - r)
+
+
+def decode(m, r, P, L, perms, llr, integer=False, n_threads=0, want_margin=True, want_ops=False):
+    """p-FHT-FSCL-L-P decoding of frames `llr` (F, 2^m). With integer=True the LLRs must be
+    integer valued and the whole decoder runs in int64 arithmetic.
+
+    Returns dict: cw (F,N) uint8, info (F,K) uint8, pm (F,), margin (F,), ops (F,),
+    best (F,) int32 (winning decoder).
+    """
+    lib = _load()
+    n = 1 << m
+    perms = np.ascontiguousarray(perms, dtype=np.uint16)
+    assert perms.shape[0] == P and perms.shape[2] == PERM_REC
+    if integer:
+        y = np.ascontiguousarray(llr, dtype=np.int64).reshape(-1, n)
+        pm = np.zeros(y.shape[0], dtype=np.int64)
+        fn = lib.rmo_decode_i64
+    else:
+        y = np.ascontiguousarray(llr, dtype=np.float64).reshape(-1, n)
+        pm = np.zeros(y.shape[0], dtype=np.float64)
+        fn = lib.rmo_decode_f64
+    F = y.shape[0]
+    cw = np.zeros((F, n), dtype=np.uint8)
+    info = np.zeros((F, _k(m, r)), dtype=np.uint8)
+    margin = np.zeros(F, dtype=np.float64) if want_margin else None
+    ops = np.zeros(F, dtype=np.int64) if want_ops else None
+    best = np.zeros(F, dtype=np.int32)
+    rc = fn(m, r, P, L, _ptr(perms), _ptr(y), F, n_threads, _ptr(cw), _ptr(info), _ptr(pm),
+            _ptr(margin), _ptr(ops), _ptr(best))
+    if rc != 0:
+        raise RuntimeError(f"oracle decode failed rc={rc}")
+    return {"cw": cw, "info": info, "pm": pm, "margin": margin, "ops": ops, "best": best}
+
+
+def aut_ssc(m, r, perms, llr, integer=False, n_threads=0):
+    """Aut-SSC-P: SSC decoding of P permuted copies; perms (P, 11) GA(m) records."""
+    lib = _load()
+    n = 1 << m
+    perms = np.ascontiguousarray(perms, dtype=np.uint16).reshape(-1, PERM_REC)
+    P = perms.shape[0]
+    if integer:
+        y = np.ascontiguousarray(llr, dtype=np.int64).reshape(-1, n)
+        disc = np.zeros(y.shape[0], dtype=np.int64)
+        fn = lib.rmo_aut_ssc_i64
+    else:
+        y = np.ascontiguousarray(llr, dtype=np.float64).reshape(-1, n)
+        disc = np.zeros(y.shape[0], dtype=np.float64)
+        fn = lib.rmo_aut_ssc_f64
+    F = y.shape[0]
+    cw = np.zeros((F, n), dtype=np.uint8)
+    info = np.zeros((F, _k(m, r)), dtype=np.uint8)
+    best = np.zeros(F, dtype=np.int32)
+    rc = fn(m, r, P, _ptr(perms), _ptr(y), F, n_threads, _ptr(cw), _ptr(info), _ptr(disc), _ptr(best))
+    if rc != 0:
+        raise RuntimeError(f"oracle aut-ssc failed rc={rc}")
+    return {"cw": cw, "info": info, "disc": disc, "best": best}
+
+
+def fht(a):
+    """Walsh-Hadamard transform c_k = sum_j a_j (-1)^popcount(k & j) of a length-2^s vector."""
+    lib = _load()
+    v = np.ascontiguousarray(a, dtype=np.float64).copy()
+    s = int(np.log2(v.size))
+    lib.rmo_fht_f64(_ptr(v), s)
+    return v
+
+
+def _node(fn, alpha, pm):
+    alpha = np.ascontiguousarray(alpha, dtype=np.float64)
+    L, n = alpha.shape
+    s = int(np.log2(n))
+    pm = np.ascontiguousarray(pm, dtype=np.float64)
+    parent = np.zeros(L, dtype=np.int32)
+    x = np.zeros((L, n), dtype=np.uint8)
+    pmo = np.zeros(L, dtype=np.float64)
+    rc = fn(s, L, _ptr(alpha), _ptr(pm), _ptr(parent), _ptr(x), _ptr(pmo))
+    if rc != 0:
+        raise RuntimeError("oracle node failed")
+    return parent, x, pmo
+
+
+def fhtl(alpha, pm):
+    """One FHTL node (Algorithms 3-4) on L paths: alpha (L, 2^s), pm (L,)."""
+    return _node(_load().rmo_fhtl_f64, alpha, pm)
+
+
+def spcl(alpha, pm):
+    """One SPCL node (Eqs. (2)-(6)) on L paths: alpha (L, 2^s), pm (L,)."""
+    return _node(_load().rmo_spcl_f64, alpha, pm)

@@ -1,0 +1,209 @@
+"""Pins of the CPU oracle to facts fixed by the paper and by mathematics, independent of the
+oracle's own code: a library Hadamard matrix, closed-form FHT spectra, brute-force maximum
+likelihood on small codes, the path-metric = discrepancy identity, noiseless decoding, the
+integer mode, and the frame error rates printed in the paper's figures."""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle as O
+from paper_2108_12550_gb300 import inputs as I
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _disc(llr, cw):
+    """Correlation discrepancy sum_i |y_i| [x_i != HD(y_i)] (the long path metric, Eq. (7))."""
+    return np.sum(np.abs(llr) * (cw != (llr < 0)), axis=-1)
+
+
+# ------------------------------------------------------------------ FHT (Algorithm 4) ---
+
+@pytest.mark.parametrize("s", [1, 2, 3, 5, 8])
+def test_fht_equals_sylvester_hadamard_product(s):
+    rng = np.random.default_rng(s)
+    a = rng.normal(size=1 << s)
+    # scipy's Sylvester matrix has H[k, j] = (-1)^popcount(k & j)
+    np.testing.assert_allclose(O.fht(a), scipy.linalg.hadamard(1 << s) @ a, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("s", [3, 6, 8])
+def test_fht_of_noiseless_first_order_word_has_single_peak(s):
+    n = 1 << s
+    j = np.arange(n)
+    for k in [0, 1, n - 1, n // 3]:
+        for sign in [0, 1]:
+            x = (np.array([bin(k & v).count("1") & 1 for v in j]) ^ sign)
+            c = O.fht(1.0 - 2.0 * x)
+            assert abs(c[k]) == n and (c[k] < 0) == bool(sign)
+            assert np.count_nonzero(c) == 1
+
+
+def _rm1_codewords(s):
+    n = 1 << s
+    j = np.arange(n)
+    words = []
+    for k in range(n):
+        base = np.array([bin(k & v).count("1") & 1 for v in j], dtype=np.uint8)
+        words.append((k, 0, base))
+        words.append((k, 1, base ^ 1))
+    return words
+
+
+@pytest.mark.parametrize("s", [3, 4, 6])
+def test_fhtl_single_path_is_ml_and_top_list_by_brute_force(s):
+    rng = np.random.default_rng(10 + s)
+    words = _rm1_codewords(s)
+    for trial in range(20):
+        a = rng.normal(size=(1, 1 << s)) * 2
+        # L = 1: FHT decoding is maximum likelihood for RM(1, s)
+        _, x, pm = O.fhtl(a, np.zeros(1))
+        d = [(_disc(a[0], w), k, sg) for k, sg, w in words]
+        best = min(d)
+        assert abs(pm[0] - best[0]) < 1e-9 and abs(_disc(a[0], x[0]) - best[0]) < 1e-9
+        # L = 4: the list holds the 4 best codewords among "best sign per index k"
+        L = 4
+        _, x4, pm4 = O.fhtl(np.repeat(a, 1, axis=0).repeat(1, axis=0)[:1].repeat(L, axis=0) * 0 + a,
+                             np.array([0.0, 1e9, 1e9, 1e9]))
+        per_k = {}
+        for dv, k, sg in d:
+            per_k[k] = min(per_k.get(k, (np.inf,)), (dv, k, sg))
+        expect = sorted(per_k.values())[:L]
+        np.testing.assert_allclose(pm4, [e[0] for e in expect], atol=1e-9)
+        for q in range(L):
+            assert abs(_disc(a[0], x4[q]) - pm4[q]) < 1e-9  # Eq. (7) = Eq. (8)
+
+
+def _even_words(n):
+    out = []
+    for v in range(1 << n):
+        w = np.array([(v >> i) & 1 for i in range(n)], dtype=np.uint8)
+        if w.sum() % 2 == 0:
+            out.append(w)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("s,L", [(3, 1), (3, 2), (3, 4), (3, 8), (4, 1), (4, 4), (4, 8)])
+def test_spcl_single_path_lists_the_best_parity_words(s, L):
+    """L = 1 is the Wagner rule; with one live path the SPCL list (tau = min(L, N-1)
+    splits) is the L most likely even-weight words, found here by enumeration."""
+    rng = np.random.default_rng(100 + 7 * s + L)
+    words = _even_words(1 << s)
+    for trial in range(30):
+        a = rng.normal(size=(1, 1 << s)) * 3
+        alpha = np.repeat(a, L, axis=0)
+        pm0 = np.full(L, 1e9)
+        pm0[0] = 0.0  # only path 0 is live
+        _, x, pm = O.spcl(alpha, pm0)
+        d = np.sort(_disc(a[0], words))
+        k = min(L, len(words))
+        np.testing.assert_allclose(pm[:k], d[:k], atol=1e-9)
+        for q in range(k):
+            assert x[q].sum() % 2 == 0 and abs(_disc(a[0], x[q]) - pm[q]) < 1e-9
+
+
+# ----------------------------------------------------------- whole decoder (Alg. 2-5) ---
+
+CODES = [(4, 2), (5, 2), (5, 3), (6, 2), (6, 3), (7, 2), (9, 2), (9, 3)]
+
+
+@pytest.mark.parametrize("m,r", CODES)
+@pytest.mark.parametrize("L", [1, 2, 4, 8])
+def test_noiseless_frames_decode_exactly(m, r, L):
+    P = 3
+    perms = I.perm_table(m, r, P, L, seed=m * 100 + r * 10 + L)
+    nl = I.noiseless_frames(m, r, 6, seed=L)
+    out = O.decode(m, r, P, L, perms, nl["llr"])
+    assert np.array_equal(out["info"], nl["u"]) and np.array_equal(out["cw"], nl["x"])
+    assert np.all(np.abs(out["pm"]) < 1e-9)
+
+
+@pytest.mark.parametrize("m,r,P,L,eb", [(5, 2, 4, 2, 2.0), (7, 2, 8, 4, 2.0), (9, 2, 4, 4, 2.0),
+                                        (5, 3, 2, 8, 3.0), (9, 3, 2, 8, 3.0)])
+def test_path_metric_equals_discrepancy(m, r, P, L, eb):
+    """For min-sum f and exact g the path metric telescopes to the correlation discrepancy of
+    the decoded word in the channel domain; permutations preserve it."""
+    perms = I.perm_table(m, r, P, L, seed=3)
+    fr = I.make_frames(m, r, 60, eb, seed=m + r)
+    out = O.decode(m, r, P, L, perms, fr["llr"])
+    D = _disc(fr["llr"], out["cw"])
+    np.testing.assert_allclose(out["pm"], D, rtol=1e-12, atol=1e-9)
+    qi = I.quantize_i8(fr["llr"]).astype(np.int64)
+    oi = O.decode(m, r, P, L, perms, qi, integer=True)
+    assert np.array_equal(oi["pm"], _disc(qi, oi["cw"]).astype(np.int64))
+
+
+@pytest.mark.parametrize("m,r,P,L", [(5, 2, 4, 2), (7, 2, 8, 4), (9, 3, 2, 8)])
+def test_integer_mode_equals_fp64_on_integer_llrs(m, r, P, L):
+    perms = I.perm_table(m, r, P, L, seed=21)
+    fr = I.make_frames(m, r, 80, 1.5, seed=22)
+    q = I.quantize_i8(fr["llr"])
+    a = O.decode(m, r, P, L, perms, q.astype(np.int64), integer=True)
+    b = O.decode(m, r, P, L, perms, q.astype(np.float64))
+    assert np.array_equal(a["cw"], b["cw"]) and np.array_equal(a["pm"].astype(np.float64), b["pm"])
+    assert np.array_equal(a["best"], b["best"])
+
+
+@pytest.mark.parametrize("m,r", [(4, 2), (5, 2)])
+def test_brute_force_ml(m, r):
+    """Exhaustive ML over all 2^K codewords (2^11 for RM(2,4), 2^16 for RM(2,5)): the
+    decoder never beats ML, and with a large list it reaches ML on nearly every frame."""
+    n, k = I.rm_dims(m, r)
+    u = ((np.arange(1 << k)[:, None] >> np.arange(k)) & 1).astype(np.uint8)
+    book = I.encode(u, m, r).astype(np.float64)
+    fr = I.make_frames(m, r, 300, 1.0, seed=5)
+    corr = fr["llr"] @ (1 - 2 * book).T  # maximise correlation = minimise discrepancy
+    ml = book[np.argmax(corr, axis=1)].astype(np.uint8)
+    d_ml = _disc(fr["llr"], ml)
+    P, L = 8, 8
+    out = O.decode(m, r, P, L, I.perm_table(m, r, P, L, seed=9), fr["llr"])
+    d_dec = _disc(fr["llr"], out["cw"])
+    assert np.all(d_dec >= d_ml - 1e-9)
+    hit = np.mean(np.abs(d_dec - d_ml) < 1e-9)
+    assert hit >= 0.97, hit
+    # a single decoder with L = 1 is clearly weaker than the big list (sanity of the list)
+    o1 = O.decode(m, r, 1, 1, I.perm_table(m, r, 1, 1, seed=9), fr["llr"])
+    assert np.mean(np.abs(_disc(fr["llr"], o1["cw"]) - d_ml) < 1e-9) < hit
+
+
+def test_ssc_baseline_properties():
+    m, r = 7, 2
+    perms = np.stack([I.sample_ga(m, 4, 0, q) for q in range(16)])
+    nl = I.noiseless_frames(m, r, 5, seed=2)
+    out = O.aut_ssc(m, r, perms, nl["llr"])
+    assert np.array_equal(out["info"], nl["u"])
+    fr = I.make_frames(m, r, 100, 2.0, seed=8)
+    out = O.aut_ssc(m, r, perms, fr["llr"])
+    np.testing.assert_allclose(out["disc"], _disc(fr["llr"], out["cw"]), atol=1e-9)
+    # more permutations can only lower the selected discrepancy (it is a minimum over them)
+    o4 = O.aut_ssc(m, r, perms[:4], fr["llr"])
+    assert np.all(out["disc"] <= o4["disc"] + 1e-12)
+
+
+def _paper_rows():
+    rows = []
+    for line in open(os.path.join(GOLD, "paper_fer.txt")):
+        if line.strip() and not line.startswith("#"):
+            t = line.split()
+            rows.append((int(t[0]), int(t[1]), t[2], int(t[3]), int(t[4]), float(t[5]), float(t[6]), " ".join(t[7:])))
+    return rows
+
+
+@pytest.mark.parametrize("row", _paper_rows(), ids=lambda r: r[7].replace(" ", "_") + f"@{r[5]}dB")
+def test_fer_matches_paper_figures(row):
+    """Monte-Carlo FER against the values printed in the paper's Figs. 4 and 6. The band
+    (a factor 2.2 either way) is wide enough for the sample size and for the unstated
+    Eb/N0 convention, narrow enough to catch a wrong list rule or a dropped term."""
+    m, r, dec, P, L, eb, fer_paper, _ = row
+    n_frames = int(min(16000, max(1500, 30 / fer_paper)))  # about 30 expected errors
+    fr = I.make_frames(m, r, n_frames, eb, seed=2024)
+    if dec == "pfht":
+        out = O.decode(m, r, P, L, I.perm_table(m, r, P, L, seed=31), fr["llr"], want_margin=False)
+    else:
+        perms = np.stack([I.sample_ga(m, 31, 0, q) for q in range(P)])
+        out = O.aut_ssc(m, r, perms, fr["llr"])
+    errs = int(np.sum(np.any(out["info"] != fr["u"], axis=1)))
+    fer = errs / n_frames
+    assert fer_paper / 2.2 <= fer <= fer_paper * 2.2, (fer, errs, n_frames, fer_paper)
