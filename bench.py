@@ -1,0 +1,272 @@
+"""Throughput benchmark of batched p-FHT-FSCL-L-P decoding on GB300.
+
+One step = one rmdec_decode call over a batch of synthetic RM(2,9) frames (BPSK over AWGN at
+Eb/N0 = 2.25 dB, where the P=20, L=4 decoder's FER is about 1e-4), with the LLRs resident in
+HBM. Prints one JSON line (see the keys below). ``--impl reference`` times the CPU oracle on
+the host cores instead (the reference arm of this method: there is no other implementation).
+
+Under torchrun (N > 1 GPUs) every rank decodes its own batch (frames shard with no data-path
+exchange: weak scaling); rank 0 prints the whole-job throughput from the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2108_12550_gb300 import inputs as I  # noqa: E402
+from paper_2108_12550_gb300 import opcount  # noqa: E402
+
+WORKLOADS = {
+    # name: (m, r, P, L, EbN0 dB, frames per step)
+    "rm29_p20_l4": (9, 2, 20, 4, 2.25, 1 << 18),
+    "rm27_p8_l4": (7, 2, 8, 4, 3.0, 1 << 20),
+    "rm25_p4_l2": (5, 2, 4, 2, 3.0, 1 << 21),
+    "rm39_p16_l8": (9, 3, 16, 8, 4.0, 1 << 16),
+}
+METRIC = "frames/s RM(2,9) P=20 L=4 at FER~1e-4 Eb/N0"
+SMS = 152
+LANES_PER_SM = 128
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return pk, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _frames(m, r, nf, ebn0, seed, chunk=1 << 16):
+    """Seeded BPSK/AWGN frames (FP32 LLRs) and their messages, generated in chunks."""
+    n, k = I.rm_dims(m, r)
+    llr = np.empty((nf, n), dtype=np.float32)
+    u = np.empty((nf, k), dtype=np.uint8)
+    for c0 in range(0, nf, chunk):
+        c1 = min(nf, c0 + chunk)
+        fr = I.make_frames(m, r, c1 - c0, ebn0, seed=seed * 1000003 + c0)
+        llr[c0:c1] = fr["llr"]
+        u[c0:c1] = fr["u"]
+    return llr, u
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                self.rows.append(f)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def cpu_baseline(m, r, P, L, ebn0, n_frames, seed=3):
+    """Times the CPU oracle (all host cores) on a bounded sample of the same workload."""
+    import oracle
+
+    llr, _ = _frames(m, r, n_frames, ebn0, seed)
+    perms = I.perm_table(m, r, P, L, seed=1)
+    cores = os.cpu_count() or 1
+    oracle.decode(m, r, P, L, perms, llr[: min(64, n_frames)].astype(np.float64), want_margin=False)
+    t0 = time.perf_counter()
+    oracle.decode(m, r, P, L, perms, llr.astype(np.float64), n_threads=cores, want_margin=False)
+    dt = time.perf_counter() - t0
+    return {"value": n_frames / dt, "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n_frames} frames of the same workload (FP64 oracle, {cores} threads)"}
+
+
+def run_reference(args, wl):
+    m, r, P, L, ebn0, _ = wl
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_step = args.ref_frames
+    import oracle
+
+    llr, _ = _frames(m, r, per_step, ebn0, seed=5)
+    perms = I.perm_table(m, r, P, L, seed=1)
+    y = llr.astype(np.float64)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle.decode(m, r, P, L, perms, y[: max(1, per_step // 8)], n_threads=cores, want_margin=False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.decode(m, r, P, L, perms, y, n_threads=cores, want_margin=False)
+    dt = time.perf_counter() - t0
+    v = per_step * args.steps / dt
+    line = {"metric": METRIC, "value": v, "unit": "frames/s", "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "m": m, "r": r, "P": P, "L": L,
+                                            "ebn0_db": ebn0, "frames_per_step": per_step},
+            "cpu_baseline": {"value": v, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} frames per step, FP64 oracle on {cores} host threads"},
+            "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="rm29_p20_l4", choices=sorted(WORKLOADS))
+    ap.add_argument("--frames", type=int, default=0, help="frames per step (default per workload)")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "i8", "f16", "i16"])
+    ap.add_argument("--cpu-frames", type=int, default=1500, help="CPU-baseline sample size")
+    ap.add_argument("--ref-frames", type=int, default=1000, help="frames per reference-arm step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2108_12550_gb300 as pkg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    m, r, P, L, ebn0, nf_default = wl
+    nf = args.frames or nf_default
+    n, k = I.rm_dims(m, r)
+    llr_np, u_np = _frames(m, r, nf, ebn0, seed=100 + rank)
+    if args.dtype == "i8":
+        llr_np = I.quantize_i8(llr_np)
+    elif args.dtype == "i16":
+        llr_np = np.clip(np.rint(llr_np * 256), -32767, 32767).astype(np.int16)
+    elif args.dtype == "f16":
+        llr_np = I.to_f16(llr_np)
+    dec = pkg.Decoder(m, r, P, L, perm_seed=1, dtype=args.dtype)
+    x = torch.from_numpy(llr_np).cuda()
+    out = torch.empty((nf, dec.kw), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (also builds device tables)
+    for _ in range(args.warmup):
+        dec.decode(x, out, stream)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            dec.decode(x, out, stream)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = nf * world / (ms_max * 1e-3)
+
+    # correctness side-channel: frame error rate of the timed batch vs the transmitted messages
+    got = pkg.unpack_bits(out.cpu().numpy(), k)
+    fer = float(np.mean(np.any(got != u_np, axis=1)))
+
+    # end to end through the host entry point: pinned host LLRs in, information bits out
+    host_in = torch.from_numpy(llr_np).pin_memory()
+    host_out = torch.empty((nf, dec.kw), dtype=torch.int32).pin_memory()
+    dec.decode_host(host_in, host_out, stream)
+    barrier()
+    e0 = time.perf_counter()
+    e_steps = max(1, min(args.steps, 5))
+    for _ in range(e_steps):
+        dec.decode_host(host_in, host_out, stream)
+    barrier()
+    e_ms = (time.perf_counter() - e0) / e_steps * 1e3
+    te = torch.tensor([e_ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e_value = nf * world / (float(te.item()) * 1e-3)
+
+    pk, src = _peaks()
+    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    ops = opcount.ops_per_frame(m, r, P, L)
+    peak_ops = SMS * LANES_PER_SM * sm_mhz * 1e6  # one ALU op per lane per clock
+    achieved = ops * nf / (ms * 1e-3)
+    line = {
+        "metric": METRIC if args.workload == "rm29_p20_l4" else f"frames/s {args.workload}",
+        "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": args.workload, "m": m, "r": r, "P": P, "L": L, "n": n, "k": k,
+                   "ebn0_db": ebn0, "frames_per_step": nf, "l2": "inputs larger than L2 "
+                   f"({llr_np.nbytes / 2**20:.0f} MiB of LLRs per step)", "parallelism": f"replicas{world}"},
+        "info_gbit_s": value * k / 1e9,
+        "fer_of_timed_batch": fer,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+                     "frac": achieved / peak_ops, "traffic": None,
+                     "peak_source": f"{SMS} SMs x {LANES_PER_SM} lanes x {sm_mhz:.0f} MHz ({src} max SM clock)",
+                     "ops_per_frame": ops},
+        "e2e": {"value": e_value, "unit": "frames/s", "h2d_bytes_per_step": int(llr_np.nbytes),
+                "d2h_bytes_per_step": int(nf * dec.kw * 4)},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(m, r, P, L, ebn0, args.cpu_frames)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

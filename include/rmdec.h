@@ -1,0 +1,133 @@
+/*
+ * rmdec — batched GPU decoding of Reed-Muller codes RM(r, m) with permuted fast
+ * successive-cancellation list decoding and the fast Hadamard transform (p-FHT-FSCL-L-M),
+ * after Doan, Hashemi and Gross, "Successive-Cancellation Decoding of Reed-Muller Codes
+ * with Fast Hadamard Transform" (arXiv 2108.12550), Algorithms 2-5.
+ *
+ * Plain C ABI. Pointers are host or device memory as stated per argument; no handle keeps
+ * a caller pointer after the call's stream work completes. No C++ exception crosses this
+ * boundary. Every entry point returns an rmdec_status; on failure nothing was launched
+ * (unless stated otherwise) and rmdec_last_error(h) describes the failure.
+ *
+ * Notation: N = 2^m code length, K = sum_{i<=r} C(m, i) information bits,
+ * P = number of parallel decoders (the paper's M, Algorithm 5), L = list size.
+ * Bit layouts: bit j of a packed bit vector is bit (j % 32) of 32-bit word j / 32.
+ */
+#ifndef RMDEC_H
+#define RMDEC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rmdec_ctx *rmdec_t;
+
+typedef enum {
+    RMDEC_OK = 0,
+    RMDEC_EINVAL = -1,      /* bad argument or unsupported (m, r, P, L) combination */
+    RMDEC_ENOMEM = -2,      /* device or host allocation failed */
+    RMDEC_ECUDA = -3,       /* a CUDA runtime call failed (message in rmdec_last_error) */
+    RMDEC_EBUSY = -4,       /* rmdec_poll: the ticket's work has not finished yet */
+    RMDEC_ETIMEDOUT = -5,   /* rmdec_poll: still running when the timeout expired */
+    RMDEC_EDEVICE = -6,     /* no usable CUDA device */
+} rmdec_status;
+
+/* LLR element type of the input frames.
+ * F32: IEEE single. F16: IEEE half, widened to single on load.
+ * I8 / I16: quantised LLR codes q (LLR = q * step for the caller's step). Integer inputs are
+ * decoded in exact integer arithmetic on the codes (every intermediate value is an integer
+ * below 2^24 and is represented exactly), so results, path metrics and tie-breaks are
+ * bit-identical to an exact integer decoder. Path metrics are reported in code units.
+ * I16 codes are clamped to |q| <= 2^(24-m) - 1 on load so that exactness holds. */
+typedef enum {
+    RMDEC_LLR_F32 = 0,
+    RMDEC_LLR_I8 = 1,
+    RMDEC_LLR_F16 = 2,
+    RMDEC_LLR_I16 = 3,
+} rmdec_dtype;
+
+/* Creates a p-FHT-FSCL-L-P decoder for RM(r, m) (Algorithm 5 with Algorithm 2 per decoder).
+ * Supported: 4 <= m <= 9, r in {2, 3} with r <= m - 2 (the root is a permuted node,
+ * 1 < r < m - 1), 1 <= P <= 64, L in {1, 2, 4, 8}.
+ * The affine permutations x -> Ax + b of GA(m) that Algorithm 2 draws (L initial ones and
+ * 2L candidates at each of the r - 1 permuted nodes, per decoder) are sampled on the host
+ * from perm_seed with Philox4x32-10 (counter (p, q, attempt, 'PERM'), key = perm_seed) and
+ * rejection of singular A; rmdec_get_perms returns them and rmdec_set_perms replaces them.
+ * No GPU work happens here: device state is built on the first decode.
+ * *out receives the handle (NULL on failure). */
+rmdec_status rmdec_create(rmdec_t *out, int m, int r, int P, int L, uint64_t perm_seed);
+
+/* Creates an Aut-SSC-P baseline decoder (the permuted simplified SC decoder the paper
+ * compares against, Section III-B, Table 5): SSC decoding (repetition, SPC and f/g nodes,
+ * L = 1) of each of P_ssc GA(m)-permuted copies of the frame, keeping the candidate with the
+ * smallest correlation discrepancy (earliest permutation on ties).
+ * Supported: 4 <= m <= 9, 1 <= r <= min(3, m - 2), 1 <= P_ssc <= 1024. Permutation q is drawn with
+ * counter (0x53534300, q, attempt, 'PERM'). */
+rmdec_status rmdec_create_aut_ssc(rmdec_t *out, int m, int r, int P_ssc, uint64_t perm_seed);
+
+/* Releases the handle and its device memory. Waits for the handle's outstanding work. */
+void rmdec_destroy(rmdec_t h);
+
+/* Sets the LLR element type read by the decode calls (default RMDEC_LLR_F32). */
+rmdec_status rmdec_set_dtype(rmdec_t h, rmdec_dtype t);
+
+/* Number of uint16 permutation records the handle holds (11 uint16 per record:
+ * [c_0 .. c_9, b] with c_t = A e_t; the record maps index i to b XOR sum_{t: i_t = 1} c_t).
+ * p-FHT-FSCL layout: decoder-major, per decoder L initial records then (r-1) * 2L candidate
+ * records (level j = 0 .. r-2 is the node RM(r-j, m-j), records of GA(m-j)).
+ * Aut-SSC layout: P_ssc records of GA(m). */
+rmdec_status rmdec_perm_count(rmdec_t h, int64_t *n_records);
+/* Host copies in / out of the permutation table (n_records must equal rmdec_perm_count).
+ * set_perms rejects records that are not invertible affine maps of the right size. */
+rmdec_status rmdec_get_perms(rmdec_t h, uint16_t *perms_host, int64_t n_records);
+rmdec_status rmdec_set_perms(rmdec_t h, const uint16_t *perms_host, int64_t n_records);
+
+/* Code parameters: *n = N, *k = K, *info_idx = the K information positions
+ * I = {i : popcount(i) >= m - r} in ascending order (owned by the handle). Any output
+ * pointer may be NULL. */
+rmdec_status rmdec_info(rmdec_t h, int *n, int *k, const int **info_idx);
+
+/* Decodes n_frames frames, asynchronously on `stream` (a cudaStream_t; NULL = legacy default
+ * stream). llr_dev: device, [n_frames][N] elements of the handle's dtype, row-major, 16-byte
+ * aligned. bits_out_dev: device, [n_frames][ceil(K/32)] uint32, the decoded information bits
+ * u_I in ascending order of I (u = x G^{(x)m} of the selected codeword x, Section II-A).
+ * n_frames == 0 is a no-op. The first call on a handle uploads its tables (synchronous). */
+rmdec_status rmdec_decode(rmdec_t h, const void *llr_dev, int64_t n_frames, uint32_t *bits_out_dev,
+                          void *stream);
+
+/* As rmdec_decode, plus optional per-frame diagnostics (any may be NULL), all device:
+ * cw_out_dev [n_frames][ceil(N/32)] uint32 the selected codeword x; pm_out_dev [n_frames]
+ * float its path metric (equal to its correlation discrepancy with the channel LLRs);
+ * best_out_dev [n_frames] int32 the decoder (p-FHT-FSCL) or permutation (Aut-SSC) that won. */
+rmdec_status rmdec_decode_debug(rmdec_t h, const void *llr_dev, int64_t n_frames, uint32_t *bits_out_dev,
+                                uint32_t *cw_out_dev, float *pm_out_dev, int32_t *best_out_dev, void *stream);
+
+/* End-to-end decode from and to HOST memory: copies the LLRs in, decodes, copies the bits
+ * out, all on `stream`, and returns after the stream work has completed. Pinned host
+ * buffers give full copy bandwidth; pageable ones work but are staged by the driver.
+ * Uses a handle-owned device staging area grown on demand. */
+rmdec_status rmdec_decode_host(rmdec_t h, const void *llr_host, int64_t n_frames, uint32_t *bits_out_host,
+                               void *stream);
+
+/* Asynchronous submission: enqueues rmdec_decode on `stream`, records a completion event and
+ * returns a ticket (> 0). The caller keeps the buffers alive until rmdec_poll reports
+ * completion. At most 1024 tickets may be outstanding per handle (RMDEC_EBUSY beyond). */
+rmdec_status rmdec_submit(rmdec_t h, const void *llr_dev, int64_t n_frames, uint32_t *bits_out_dev,
+                          void *stream, uint64_t *ticket);
+
+/* Waits up to timeout_us microseconds (0 = just check) for a ticket. Returns RMDEC_OK once
+ * complete (the ticket is then retired), RMDEC_EBUSY if timeout_us == 0 and not complete,
+ * RMDEC_ETIMEDOUT if the wait expired, RMDEC_EINVAL for an unknown ticket. */
+rmdec_status rmdec_poll(rmdec_t h, uint64_t ticket, int64_t timeout_us);
+
+/* Per-thread description of the last failure on this handle (or of the last failed create
+ * when h is NULL). Never NULL; valid until the next call on the same handle. */
+const char *rmdec_last_error(rmdec_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RMDEC_H */

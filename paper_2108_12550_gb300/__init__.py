@@ -1,0 +1,199 @@
+"""Python binding of librmdec: GPU p-FHT-FSCL-L-M decoding of Reed-Muller codes
+(arXiv 2108.12550) and the Aut-SSC-P baseline.
+
+This module only marshals arguments to the C ABI declared in ``include/rmdec.h``; every
+decoding step runs in the library's CUDA kernels. PyTorch supplies device memory and
+streams. Importing fails loudly if the compiled library is missing: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librmdec.so")
+
+OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEDOUT, EDEVICE = 0, -1, -2, -3, -4, -5, -6
+DTYPES = {"f32": 0, "i8": 1, "f16": 2, "i16": 3}
+PERM_REC = 11
+
+_lib = None
+
+
+class RmdecError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"rmdec status {status}: {msg}")
+        self.status = status
+
+
+def load_library():
+    """Loads librmdec.so (built by ``paper_2108_12550_gb300._build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    V, I, I64, U64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64
+    sig = {
+        "rmdec_create": ([ctypes.POINTER(V), I, I, I, I, U64], I),
+        "rmdec_create_aut_ssc": ([ctypes.POINTER(V), I, I, I, U64], I),
+        "rmdec_destroy": ([V], None),
+        "rmdec_set_dtype": ([V, I], I),
+        "rmdec_perm_count": ([V, ctypes.POINTER(I64)], I),
+        "rmdec_get_perms": ([V, V, I64], I),
+        "rmdec_set_perms": ([V, V, I64], I),
+        "rmdec_info": ([V, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.POINTER(I))], I),
+        "rmdec_decode": ([V, V, I64, V, V], I),
+        "rmdec_decode_debug": ([V, V, I64, V, V, V, V, V], I),
+        "rmdec_decode_host": ([V, V, I64, V, V], I),
+        "rmdec_submit": ([V, V, I64, V, V, ctypes.POINTER(U64)], I),
+        "rmdec_poll": ([V, U64, I64], I),
+        "rmdec_last_error": ([V], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+class Decoder:
+    """A decoder handle. algo='pfht' (p-FHT-FSCL-L-P, Algorithm 5) or 'autssc' (Aut-SSC-P)."""
+
+    def __init__(self, m, r, P, L=1, perm_seed=0, dtype="f32", perms=None, algo="pfht"):
+        lib = load_library()
+        self._lib = lib
+        h = ctypes.c_void_p()
+        if algo == "pfht":
+            st = lib.rmdec_create(ctypes.byref(h), m, r, P, L, perm_seed)
+        elif algo == "autssc":
+            st = lib.rmdec_create_aut_ssc(ctypes.byref(h), m, r, P, perm_seed)
+        else:
+            raise ValueError(algo)
+        if st != OK:
+            raise RmdecError(st, lib.rmdec_last_error(None).decode())
+        self._h = h
+        self.m, self.r, self.P, self.L, self.algo = m, r, P, (L if algo == "pfht" else 1), algo
+        n, k = ctypes.c_int(), ctypes.c_int()
+        idx = ctypes.POINTER(ctypes.c_int)()
+        self._check(lib.rmdec_info(h, ctypes.byref(n), ctypes.byref(k), ctypes.byref(idx)))
+        self.n, self.k = n.value, k.value
+        self.info_idx = np.array([idx[i] for i in range(self.k)], dtype=np.int64)
+        self.kw = (self.k + 31) // 32
+        self.nw = max(1, self.n // 32)
+        self.dtype = None
+        self.set_dtype(dtype)
+        if perms is not None:
+            self.set_perms(perms)
+
+    def _check(self, st):
+        if st != OK:
+            raise RmdecError(st, self._lib.rmdec_last_error(self._h).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.rmdec_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_dtype(self, dtype):
+        self._check(self._lib.rmdec_set_dtype(self._h, DTYPES[dtype]))
+        self.dtype = dtype
+
+    def perm_count(self):
+        n = ctypes.c_int64()
+        self._check(self._lib.rmdec_perm_count(self._h, ctypes.byref(n)))
+        return n.value
+
+    def get_perms(self):
+        n = self.perm_count()
+        out = np.zeros((n, PERM_REC), dtype=np.uint16)
+        self._check(self._lib.rmdec_get_perms(self._h, out.ctypes.data, n))
+        return out
+
+    def set_perms(self, perms):
+        a = np.ascontiguousarray(perms, dtype=np.uint16).reshape(-1, PERM_REC)
+        self._check(self._lib.rmdec_set_perms(self._h, a.ctypes.data, a.shape[0]))
+
+    def _alloc_bits(self, F, out):
+        import torch
+        if out is None:
+            out = torch.empty((F, self.kw), dtype=torch.int32, device="cuda")
+        return out
+
+    def decode(self, llr, out=None, stream=None):
+        """llr: CUDA tensor [F, n] of the handle's dtype. Returns int32 [F, ceil(k/32)]."""
+        F = llr.shape[0]
+        out = self._alloc_bits(F, out)
+        self._check(self._lib.rmdec_decode(self._h, _ptr(llr), F, _ptr(out), _stream_ptr(stream)))
+        return out
+
+    def decode_debug(self, llr, stream=None):
+        import torch
+        F = llr.shape[0]
+        bits = self._alloc_bits(F, None)
+        cw = torch.empty((F, self.nw), dtype=torch.int32, device="cuda")
+        pm = torch.empty(F, dtype=torch.float32, device="cuda")
+        best = torch.empty(F, dtype=torch.int32, device="cuda")
+        self._check(self._lib.rmdec_decode_debug(self._h, _ptr(llr), F, _ptr(bits), _ptr(cw), _ptr(pm),
+                                                 _ptr(best), _stream_ptr(stream)))
+        return bits, cw, pm, best
+
+    def decode_host(self, llr_host, out_host, stream=None):
+        """Host-to-host decode (copies inside): llr_host/out_host are CPU tensors (pinned for speed)."""
+        self._check(self._lib.rmdec_decode_host(self._h, llr_host.data_ptr(), llr_host.shape[0],
+                                                out_host.data_ptr(), _stream_ptr(stream)))
+        return out_host
+
+    def submit(self, llr, out, stream=None):
+        t = ctypes.c_uint64()
+        self._check(self._lib.rmdec_submit(self._h, _ptr(llr), llr.shape[0], _ptr(out), _stream_ptr(stream),
+                                           ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket, timeout_us=0):
+        """Returns OK, EBUSY or ETIMEDOUT (other statuses raise)."""
+        st = self._lib.rmdec_poll(self._h, ticket, int(timeout_us))
+        if st in (OK, EBUSY, ETIMEDOUT):
+            return st
+        return self._check(st)
+
+
+def unpack_bits(words, nbits):
+    """[F, W] int32/uint32 words -> [F, nbits] uint8 (bit j = bit j%32 of word j//32)."""
+    w = np.asarray(words).astype(np.uint32)
+    bits = (w[:, :, None] >> np.arange(32, dtype=np.uint32)) & 1
+    return bits.reshape(w.shape[0], -1)[:, :nbits].astype(np.uint8)
+
+
+def pack_bits(bits):
+    """[F, nbits] 0/1 -> [F, ceil(nbits/32)] uint32."""
+    b = np.asarray(bits, dtype=np.uint32)
+    F, n = b.shape
+    W = (n + 31) // 32
+    pad = np.zeros((F, W * 32), dtype=np.uint32)
+    pad[:, :n] = b
+    return (pad.reshape(F, W, 32) << np.arange(32, dtype=np.uint32)).sum(axis=2).astype(np.uint32)

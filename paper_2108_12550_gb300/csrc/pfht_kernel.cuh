@@ -1,0 +1,798 @@
+// p-FHT-FSCL-L-M decoding kernel for RM(r, m) on sm_103a.
+//
+// Method: Doan, Hashemi, Gross, arXiv 2108.12550 — Algorithm 2 (permuted recursion),
+// Algorithms 3-4 with Eq. (8) (FHTL on RM(1, s) nodes), Eqs. (2)-(6) (SPCL on RM(s-1, s)
+// nodes) and Algorithm 5 (best of P decoders).
+//
+// Execution model. A CTA owns one frame at a time (persistent loop over frames). Its W warps
+// share the frame's LLRs in shared memory and split the P decoders round-robin; a warp runs
+// one decoder with all L list paths at once. The decoding tree is expanded at compile time
+// (template recursion over (r_v, m_v, span offset)), so every node's size, lane mapping and
+// register arrays are static. Per warp, shared memory holds one LLR buffer per tree level
+// with L slots; list reselection never copies LLRs: each path keeps, per pending ancestor
+// level, the slot index of its ancestor's LLRs (shuffled from the parent lane on every list
+// step). Decided bits of finished nodes sit in a per-path packed bit buffer (double
+// buffered; a list step copies only the words left of the current node).
+//
+// Exactness: the arithmetic is add, subtract, min, abs, negate, compare and multiply by 1/2.
+// On integer-valued LLRs below 2^24 / 2^m every intermediate value is an exactly
+// represented integer, so the integer input types decode bit-exactly.
+#pragma once
+
+#include <cstdint>
+#include <type_traits>
+
+#include <cuda_fp16.h>
+
+namespace rmdec_dev {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kRec = 11;  // uint16 per permutation record: [c_0..c_9, b]
+
+enum InType { IN_F32 = 0, IN_I8 = 1, IN_F16 = 2, IN_I16 = 3 };
+
+__host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
+__host__ __device__ constexpr int cilog2(int x) { return x <= 1 ? 0 : 1 + cilog2(x >> 1); }
+
+struct LaunchArgs {
+    const void* llr;
+    int dtype;
+    float qclamp;  // |code| clamp for I16 inputs
+    int64_t n_frames;
+    int P;
+    const uint16_t* recs;  // device records, P * NREC * kRec
+    const uint16_t* info;  // K information positions
+    int K;
+    uint32_t* info_out;  // [F][ceil(K/32)]
+    uint32_t* cw_out;    // [F][ceil(N/32)] or null
+    float* pm_out;       // [F] or null
+    int32_t* best_out;   // [F] or null
+};
+
+// Shared-memory layout of one decoder configuration.
+template <int M, int R, int L>
+struct Cfg {
+    static constexpr int N = 1 << M;
+    static constexpr int NW = N >= 32 ? N / 32 : 1;
+    static constexpr int NLEV = R - 1;           // permuted nodes: levels M, M-1, ..., M-R+2
+    static constexpr int NREC = 2 * L * NLEV;    // device records per decoder
+    static constexpr int MIN_DEEP = M - R + 2;   // lowest permuted level
+
+    static __host__ __device__ constexpr int lanes(int s) { return cmin(32 / L, 1 << s); }
+    static __host__ __device__ constexpr int stride(int s) {
+        return (1 << s) + (((1 << s) >= 32) ? lanes(s) : 0);
+    }
+    static __host__ __device__ constexpr int lvl_floats(int s) { return L * stride(s); }
+    static __host__ __device__ constexpr int lvl_off(int s) {  // main buffers, levels 2..M-1
+        int o = 0;
+        for (int t = 2; t < s; t++) o += lvl_floats(t);
+        return o;
+    }
+    static constexpr int MAIN_FLOATS = lvl_off(M);
+    static __host__ __device__ constexpr bool deep_perm(int s) { return s < M && s >= MIN_DEEP; }
+    static __host__ __device__ constexpr int alt_off(int s) {  // second buffer of permuted levels
+        int o = MAIN_FLOATS;
+        for (int t = MIN_DEEP; t < s; t++) o += lvl_floats(t);
+        return o;
+    }
+    static constexpr int ALPHA_FLOATS = alt_off(M);
+    static constexpr int BITS_WORDS = 2 * L * NW;  // double-buffered per-path bit buffers
+    // warp area: alpha | bits | xtmp (NW) | best codeword (NW) | spc order (L*32 bytes)
+    static constexpr int OFF_BITS = ALPHA_FLOATS * 4;
+    static constexpr int OFF_XTMP = OFF_BITS + BITS_WORDS * 4;
+    static constexpr int OFF_BEST = OFF_XTMP + NW * 4;
+    static constexpr int OFF_SPC = OFF_BEST + NW * 4;
+    static constexpr int WARP_BYTES = ((OFF_SPC + L * 32) + 15) / 16 * 16;
+    static __host__ constexpr int fixed_bytes(int P, int K, int W) {
+        // records, info positions, frame LLRs, per-warp (pm, p) reduction slots
+        return ((P * NREC * kRec * 2 + K * 2 + 15) / 16) * 16 + N * 4 + W * 8;
+    }
+};
+
+struct Warp {
+    float* alpha;       // this warp's LLR buffers
+    uint32_t* bits;     // 2 x L x NW
+    uint32_t* xtmp;     // NW scratch
+    uint32_t* best;     // NW: this warp's best codeword so far
+    uint8_t* spc;       // L x 32 SPC order scratch
+    const float* y;     // frame LLRs
+    const uint16_t* rec;  // this decoder's NREC records
+    int lane;
+    int bsel;           // current bit buffer (warp uniform)
+};
+
+template <int M>
+struct PState {
+    float pm;            // path metric
+    int rootc;           // root candidate (composed permutation) this path descends from
+    int slot[M + 1];     // per pending level: slot of the ancestor's LLRs
+    int selc[M + 1];     // per deeper permuted level: chosen candidate (pi*)
+};
+
+__device__ __forceinline__ float fminsum(float a, float b) {
+    // f(a, b) = min(|a|, |b|) sgn(a) sgn(b) (Section II-B), zero if either input is zero
+    float m = fminf(fabsf(a), fabsf(b));
+    float r = ((__float_as_uint(a) ^ __float_as_uint(b)) & 0x80000000u) ? -m : m;
+    return (a == 0.f || b == 0.f) ? 0.f : r;
+}
+
+// i -> b ^ A v(i) of a record, for i with at most s significant bits
+__device__ __forceinline__ int ga_apply(const uint16_t* r, int s, int i) {
+    int v = r[10];
+#pragma unroll
+    for (int t = 0; t < 10; t++)
+        if (t < s && ((i >> t) & 1)) v ^= r[t];
+    return v;
+}
+// low part for i = lane + 32 * t: b ^ A (lane), using columns 0..min(5, s)-1
+__device__ __forceinline__ int ga_lane_base(const uint16_t* r, int s, int lane) {
+    int v = r[10];
+#pragma unroll
+    for (int t = 0; t < 5; t++)
+        if (t < s && ((lane >> t) & 1)) v ^= r[t];
+    return v;
+}
+// high part A (32 t) using columns 5..s-1
+__device__ __forceinline__ int ga_hi(const uint16_t* r, int s, int t32) {
+    int v = 0;
+#pragma unroll
+    for (int b = 0; b < 5; b++)
+        if (b + 5 < s && ((t32 >> b) & 1)) v ^= r[5 + b];
+    return v;
+}
+__device__ __forceinline__ int insert_zero(int x, int h) {  // insert a 0 bit at position h
+    return ((x >> h) << (h + 1)) | (x & ((1 << h) - 1));
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+    return v;
+}
+
+template <int M, int R, int L>
+struct Decoder {
+    using C = Cfg<M, R, L>;
+    static constexpr int N = C::N;
+    static constexpr int NW = C::NW;
+
+    __device__ static uint32_t* bitbuf(Warp& w, int sel, int path) { return w.bits + (sel * L + path) * NW; }
+
+    // ---------------------------------------------------------------- list step ---
+    // New path l (lane l < L) descends from `parent`; copies path state and the decided bits
+    // left of span offset OFF. PEND: bit s set if the node at level s awaits its right child.
+    template <int OFF, unsigned PEND>
+    __device__ static void reselect(Warp& w, PState<M>& ps, int parent, float newpm) {
+        const int par = w.lane < L ? parent : 0;
+        ps.rootc = __shfl_sync(kFull, ps.rootc, par);
+#pragma unroll
+        for (int s = 2; s < M; s++) {
+            if ((PEND >> s) & 1) ps.slot[s] = __shfl_sync(kFull, ps.slot[s], par);
+            if (C::deep_perm(s)) ps.selc[s] = __shfl_sync(kFull, ps.selc[s], par);
+        }
+        ps.pm = newpm;
+        constexpr int CW = (OFF + 31) / 32;
+        if constexpr (CW > 0) {
+            __syncwarp();
+            constexpr int TOT = L * CW;
+#pragma unroll
+            for (int it = 0; it < (TOT + 31) / 32; it++) {
+                const int idx = w.lane + 32 * it;
+                const int l = idx < TOT ? idx / CW : 0;
+                const int pl = __shfl_sync(kFull, par, l);
+                if (idx < TOT) {
+                    const int wd = idx % CW;
+                    bitbuf(w, w.bsel ^ 1, l)[wd] = bitbuf(w, w.bsel, pl)[wd];
+                }
+            }
+            w.bsel ^= 1;
+            __syncwarp();
+        }
+    }
+
+    // Writes `nb` (<= 32) bits `v` of path lane (< L) at span offset OFF (RMW of one word).
+    template <int OFF, int NB>
+    __device__ static void put_small_bits(Warp& w, unsigned v) {
+        static_assert(NB <= 32 && (OFF % NB) == 0, "small span");
+        if (w.lane < L) {
+            uint32_t* wd = bitbuf(w, w.bsel, w.lane) + OFF / 32;
+            const unsigned mask = (NB == 32 ? 0xffffffffu : ((1u << NB) - 1u)) << (OFF % 32);
+            *wd = (*wd & ~mask) | ((v << (OFF % 32)) & mask);
+        }
+        __syncwarp();
+    }
+
+    // ------------------------------------------------------------- FHTL leaf ---
+    // RM(1, S) node (Algorithms 3-4): per path the Walsh-Hadamard spectrum c of its LLRs,
+    // candidates (k, sign c_k) with PM' = PM_l + (sum|alpha| - |c_k|)/2 (Eq. (8)); the L best
+    // over all paths by (PM', l, k) survive. Ranking by (PM', l, k) over all L 2^S candidates
+    // equals the paper's per-path top-min(L, 2^S) followed by the pool sort with ordinal
+    // l*T + rank, because within one path PM' falls as |c_k| rises.
+    template <int S, int OFF, unsigned PEND>
+    __device__ static void fht_leaf(Warp& w, PState<M>& ps) {
+        constexpr int G = C::lanes(S);
+        constexpr int E = (1 << S) / G;
+        constexpr int ST = C::stride(S);
+        using Mask = typename std::conditional<(E > 32), unsigned long long, unsigned>::type;
+        const float* buf = w.alpha + C::lvl_off(S);
+        const bool act = w.lane < L * G;
+        const int l = act ? w.lane / G : 0;
+        const int g = w.lane % G;
+        float v[E];
+#pragma unroll
+        for (int e = 0; e < E; e++) v[e] = act ? buf[l * ST + g + G * e] : 0.f;
+        float A = 0.f;
+#pragma unroll
+        for (int e = 0; e < E; e++) A += fabsf(v[e]);
+#pragma unroll
+        for (int d = 1; d < G; d <<= 1) A += __shfl_xor_sync(kFull, A, d);
+        // butterflies (u, w) -> (u + w, u - w) over the register bits of the index ...
+#pragma unroll
+        for (int h = 1; h < E; h <<= 1)
+#pragma unroll
+            for (int e = 0; e < E; e++)
+                if (!(e & h)) {
+                    const float a = v[e], b = v[e + h];
+                    v[e] = a + b;
+                    v[e + h] = a - b;
+                }
+        // ... and over the lane bits
+#pragma unroll
+        for (int d = 1; d < G; d <<= 1)
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                const float o = __shfl_xor_sync(kFull, v[e], d);
+                v[e] = (g & d) ? (o - v[e]) : (v[e] + o);
+            }
+        const float pml = __shfl_sync(kFull, ps.pm, l);
+        Mask taken = 0;
+        float babs = -1.f;
+        int be = 0;
+        bool bneg = false;
+        auto rescan = [&]() {
+            babs = -1.f;
+            be = 0;
+            bneg = false;
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                const float av = fabsf(v[e]);
+                const bool ok = !((taken >> e) & 1) && av > babs;
+                babs = ok ? av : babs;
+                be = ok ? e : be;
+                bneg = ok ? (v[e] < 0.f) : bneg;
+            }
+        };
+        rescan();
+        int my_par = 0, my_k = 0, my_neg = 0;
+        float my_pm = 0.f;
+#pragma unroll 1
+        for (int q = 0; q < L; q++) {
+            float cpm = (act && babs >= 0.f) ? pml + 0.5f * (A - babs) : __int_as_float(0x7f800000);
+            int cidx = (l << S) | (g + G * be);
+            int cneg = bneg ? 1 : 0;
+#pragma unroll
+            for (int d = 16; d >= 1; d >>= 1) {
+                const float opm = __shfl_xor_sync(kFull, cpm, d);
+                const int oidx = __shfl_xor_sync(kFull, cidx, d);
+                const int oneg = __shfl_xor_sync(kFull, cneg, d);
+                const bool take = (opm < cpm) || (opm == cpm && oidx < cidx);
+                cpm = take ? opm : cpm;
+                cidx = take ? oidx : cidx;
+                cneg = take ? oneg : cneg;
+            }
+            if (w.lane == q) {
+                my_pm = cpm;
+                my_par = cidx >> S;
+                my_k = cidx & ((1 << S) - 1);
+                my_neg = cneg;
+            }
+            const int wk = cidx & ((1 << S) - 1);
+            const int owner = (cidx >> S) * G + (wk % G);
+            if (w.lane == owner) {
+                taken |= Mask(1) << (wk / G);
+                rescan();
+            }
+        }
+        reselect<OFF, PEND>(w, ps, my_par, my_pm);
+        // decided bits x_j = <k, j> xor sign over the span
+        constexpr int NB = 1 << S;
+        if constexpr (NB >= 32) {
+            constexpr int WPP = NB / 32;
+            constexpr int TOT = L * WPP;
+#pragma unroll
+            for (int it = 0; it < (TOT + 31) / 32; it++) {
+                const int idx = w.lane + 32 * it;
+                const int q = idx < TOT ? idx / WPP : 0;
+                const int kq = __shfl_sync(kFull, my_k, q);
+                const int nq = __shfl_sync(kFull, my_neg, q);
+                if (idx < TOT) {
+                    const int wd = idx % WPP;
+                    unsigned pat = 0;
+#pragma unroll
+                    for (int t = 0; t < 5; t++) {
+                        const unsigned mt = t == 0 ? 0xAAAAAAAAu : t == 1 ? 0xCCCCCCCCu : t == 2 ? 0xF0F0F0F0u
+                                           : t == 3 ? 0xFF00FF00u : 0xFFFF0000u;
+                        if ((kq >> t) & 1) pat ^= mt;
+                    }
+                    if ((__popc((kq >> 5) & wd) & 1) ^ nq) pat = ~pat;
+                    bitbuf(w, w.bsel, q)[OFF / 32 + wd] = pat;
+                }
+            }
+            __syncwarp();
+        } else {
+            unsigned pat = 0;
+#pragma unroll
+            for (int j = 0; j < NB; j++) pat |= (unsigned)((__popc(my_k & j) & 1) ^ my_neg) << j;
+            put_small_bits<OFF, NB>(w, pat);
+        }
+    }
+
+    // ------------------------------------------------------------- SPCL leaf ---
+    // RM(S-1, S) node (Eqs. (2)-(6)): parity, PM += p |alpha_lrb|, then tau = min(L, 2^S - 1)
+    // list splits on the next least reliable positions (flip cost |alpha_i| + (1-2p)|alpha_lrb|,
+    // each a 2L -> L selection by (PM, 2l + flip)), finally the least reliable bit restores
+    // even parity.
+    template <int S, int OFF, unsigned PEND>
+    __device__ static void spc_leaf(Warp& w, PState<M>& ps) {
+        constexpr int NS = 1 << S;
+        static_assert(NS <= 32, "SPC node larger than a warp word");
+        constexpr int TAU = cmin(L, NS - 1);
+        constexpr int ST = C::stride(S);
+        const float* buf = w.alpha + C::lvl_off(S);
+        // reliability order of every path's positions: (|alpha|, position) ascending
+#pragma unroll
+        for (int it = 0; it < (L * NS + 31) / 32; it++) {
+            const int idx = w.lane + 32 * it;
+            if (idx < L * NS) {
+                const int l = idx / NS, i = idx % NS;
+                const float* a = buf + l * ST;
+                const float ai = fabsf(a[i]);
+                int rank = 0;
+#pragma unroll
+                for (int j = 0; j < NS; j++) {
+                    const float aj = fabsf(a[j]);
+                    rank += (aj < ai) || (aj == ai && j < i);
+                }
+                w.spc[l * 32 + rank] = (uint8_t)i;
+            }
+        }
+        __syncwarp();
+        const int me = w.lane < L ? w.lane : 0;
+        unsigned hd = 0;
+        const float* am = buf + me * ST;
+#pragma unroll
+        for (int i = 0; i < NS; i++) hd |= (am[i] < 0.f ? 1u : 0u) << i;
+        int o0 = w.spc[me * 32];
+        float lrb = fabsf(am[o0]);
+        int p = __popc(hd) & 1;
+        float pm = ps.pm + (p ? lrb : 0.f);  // Eq. (3)
+        unsigned flip = 0;
+        int orig = me;
+#pragma unroll 1
+        for (int t = 1; t <= TAU; t++) {
+            const int itp = w.spc[orig * 32 + t];
+            const float at = fabsf(buf[orig * ST + itp]);
+            const float pflip = pm + at + (p ? -lrb : lrb);  // Eq. (4)
+            const int src = w.lane < 2 * L ? (w.lane >> 1) : 0;
+            const float kpm = __shfl_sync(kFull, pm, src);
+            const float fpm = __shfl_sync(kFull, pflip, src);
+            const float cpm = (w.lane & 1) ? fpm : kpm;
+            int rank = 0;
+#pragma unroll
+            for (int c2 = 0; c2 < 2 * L; c2++) {
+                const float o = __shfl_sync(kFull, cpm, c2);
+                rank += (o < cpm) || (o == cpm && c2 < w.lane);
+            }
+            int mysrc = 0;
+#pragma unroll
+            for (int q = 0; q < L; q++) {
+                const unsigned b = __ballot_sync(kFull, w.lane < 2 * L && rank == q);
+                if (w.lane == q) mysrc = __ffs(b) - 1;
+            }
+            const int sp = mysrc >> 1;
+            const bool fl = mysrc & 1;
+            const float n_kpm = __shfl_sync(kFull, pm, sp);
+            const float n_fpm = __shfl_sync(kFull, pflip, sp);
+            const int n_orig = __shfl_sync(kFull, orig, sp);
+            const unsigned n_flip = __shfl_sync(kFull, flip, sp);
+            const int n_p = __shfl_sync(kFull, p, sp);
+            const float n_lrb = __shfl_sync(kFull, lrb, sp);
+            const int n_o0 = __shfl_sync(kFull, o0, sp);
+            const unsigned n_hd = __shfl_sync(kFull, hd, sp);
+            const int n_it = __shfl_sync(kFull, itp, sp);
+            pm = fl ? n_fpm : n_kpm;
+            orig = n_orig;
+            flip = fl ? (n_flip ^ (1u << n_it)) : n_flip;  // Eq. (5)
+            p = fl ? (n_p ^ 1) : n_p;
+            lrb = n_lrb;
+            o0 = n_o0;
+            hd = n_hd;
+        }
+        unsigned x = (hd ^ flip) & ~(1u << o0);
+        x |= (unsigned)(__popc(x) & 1) << o0;  // Eq. (6)
+        reselect<OFF, PEND>(w, ps, orig, pm);
+        put_small_bits<OFF, NS>(w, x);
+    }
+
+    // --------------------------------------------------- permutation selection ---
+    // 2L candidates: candidate c permutes the LLRs of source path c mod L; its reliability
+    // LM_c = sum_{i < N_v/2} |f(tmp_i, tmp_{i+N_v/2})| (Algorithm 2, lines 6-11). For an
+    // affine permutation, {pi(i), pi(i + N_v/2)} = {j, j ^ a} with a the image of the top
+    // index bit, so LM_c = sum over the pairs {j, j ^ a} of min(|alpha_j|, |alpha_{j^a}|),
+    // summed here with one representative j per pair (bit msb(a) clear). Returns, in lane
+    // q < L, the candidate of rank q under (LM descending, c ascending).
+    template <int S, typename Src>
+    __device__ static int select_perms(Warp& w, const uint16_t* recs, Src src) {
+        constexpr int C2 = 2 * L;
+        constexpr int HALF = 1 << (S - 1);
+        float lm[C2];
+#pragma unroll
+        for (int c = 0; c < C2; c++) {
+            const uint16_t* r = recs + c * kRec;
+            const int a = r[S - 1];
+            const int h = 31 - __clz(a);
+            const int lorg = c % L;
+            float acc = 0.f;
+#pragma unroll
+            for (int t = 0; t < (HALF + 31) / 32; t++) {
+                const int jp = w.lane + 32 * t;
+                if (jp < HALF) {
+                    const int j = insert_zero(jp, h);
+                    acc += fminf(fabsf(src(lorg, j)), fabsf(src(lorg, j ^ a)));
+                }
+            }
+            lm[c] = warp_sum(acc);
+        }
+        int mine = 0;
+#pragma unroll
+        for (int c = 0; c < C2; c++) {
+            int rank = 0;
+#pragma unroll
+            for (int c2 = 0; c2 < C2; c2++) rank += (lm[c2] > lm[c]) || (lm[c2] == lm[c] && c2 < c);
+            if (rank == w.lane) mine = c;
+        }
+        return mine;
+    }
+
+    // ------------------------------------------------------------- tree walk ---
+    template <int RR, int S, int OFF, bool ROOT, bool SPINE, unsigned PEND>
+    __device__ static void node(Warp& w, PState<M>& ps) {
+        if constexpr (RR == 1) {
+            fht_leaf<S, OFF, PEND>(w, ps);
+        } else if constexpr (RR == S - 1) {
+            spc_leaf<S, OFF, PEND>(w, ps);
+        } else {
+            constexpr bool PERM = SPINE;  // 1 < RR < S - 1 holds here
+            constexpr int H = 1 << (S - 1);
+            constexpr int STC = C::stride(S - 1);
+            float* child = w.alpha + C::lvl_off(S - 1);
+            constexpr int LEVEL = M - S;  // permuted-level index on the spine
+            const uint16_t* lrec = w.rec + LEVEL * 2 * L * kRec;
+            // LLRs of this node for path l at position j
+            // a deeper permuted node keeps its permuted copy in the level's second buffer
+            const float* nodebuf = w.alpha + ((PERM && !ROOT) ? C::alt_off(S) : C::lvl_off(S));
+            constexpr int STN = C::stride(S);
+            if constexpr (ROOT) {
+                // every path's LLRs are y, so candidate c's permuted LLRs are y through the
+                // composed permutation pi^init_{c mod L} o pi_c (one GA(m) element)
+                const int c = select_perms<S>(w, lrec, [&](int, int j) { return w.y[j]; });
+                ps.rootc = c;
+                ps.pm = 0.f;
+            } else if constexpr (PERM) {
+                const float* src = w.alpha + C::lvl_off(S);
+                const int c = select_perms<S>(w, lrec, [&](int l, int j) { return src[l * STN + j]; });
+                // path q takes source path c mod L through pi_c
+                reselect<OFF, PEND>(w, ps, c % L, ps.pm);
+                ps.selc[S] = c;
+                float* dst = w.alpha + C::alt_off(S);
+#pragma unroll 1
+                for (int q = 0; q < L; q++) {
+                    const int cq = __shfl_sync(kFull, c, q);
+                    const uint16_t* r = lrec + cq * kRec;
+                    const float* s_src = src + (cq % L) * STN;
+                    const int base = ga_lane_base(r, S, w.lane);
+#pragma unroll
+                    for (int t = 0; t < ((1 << S) + 31) / 32; t++) {
+                        const int i = w.lane + 32 * t;
+                        if (i < (1 << S)) dst[q * STN + i] = s_src[base ^ ga_hi(r, S, t)];
+                    }
+                }
+                __syncwarp();
+            }
+            if constexpr (PERM || ROOT) {
+                if (w.lane < L) ps.slot[S] = w.lane;
+            }
+            // f: left child RM(RR-1, S-1) (Algorithm 2, line 13)
+            if constexpr (ROOT) {
+#pragma unroll 1
+                for (int l = 0; l < L; l++) {
+                    const int cl = __shfl_sync(kFull, ps.rootc, l);
+                    const uint16_t* r = lrec + cl * kRec;
+                    const int a = r[S - 1];
+                    const int base = ga_lane_base(r, S - 1, w.lane);
+#pragma unroll
+                    for (int t = 0; t < (H + 31) / 32; t++) {
+                        const int i = w.lane + 32 * t;
+                        if (i < H) {
+                            const int j = base ^ ga_hi(r, S - 1, t);
+                            child[l * STC + i] = fminsum(w.y[j], w.y[j ^ a]);
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int it = 0; it < (L * H + 31) / 32; it++) {
+                    const int idx = w.lane + 32 * it;
+                    if (idx < L * H) {
+                        const int l = idx / H, i = idx % H;
+                        child[l * STC + i] = fminsum(nodebuf[l * STN + i], nodebuf[l * STN + i + H]);
+                    }
+                }
+            }
+            __syncwarp();
+            node<RR - 1, S - 1, OFF, false, SPINE, (PEND | (1u << S))>(w, ps);
+            // g: right child RM(RR, S-1) from the path's own ancestor LLRs (line 15)
+            if constexpr (ROOT) {
+#pragma unroll 1
+                for (int l = 0; l < L; l++) {
+                    const int cl = __shfl_sync(kFull, ps.rootc, l);
+                    const uint16_t* r = lrec + cl * kRec;
+                    const int a = r[S - 1];
+                    const int base = ga_lane_base(r, S - 1, w.lane);
+                    const uint32_t* bl = bitbuf(w, w.bsel, l);
+#pragma unroll
+                    for (int t = 0; t < (H + 31) / 32; t++) {
+                        const int i = w.lane + 32 * t;
+                        if (i < H) {
+                            const int j = base ^ ga_hi(r, S - 1, t);
+                            const int xb = (bl[(OFF + i) >> 5] >> ((OFF + i) & 31)) & 1;
+                            const float u = w.y[j], v = w.y[j ^ a];
+                            child[l * STC + i] = xb ? v - u : v + u;
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int it = 0; it < (L * H + 31) / 32; it++) {
+                    const int idx = w.lane + 32 * it;
+                    const int l = idx < L * H ? idx / H : 0;
+                    const int sl = __shfl_sync(kFull, ps.slot[S], l);
+                    if (idx < L * H) {
+                        const int i = idx % H;
+                        const uint32_t* bl = bitbuf(w, w.bsel, l);
+                        const int xb = (bl[(OFF + i) >> 5] >> ((OFF + i) & 31)) & 1;
+                        const float u = nodebuf[sl * STN + i], v = nodebuf[sl * STN + i + H];
+                        child[l * STC + i] = xb ? v - u : v + u;
+                    }
+                }
+            }
+            __syncwarp();
+            node<RR, S - 1, OFF + H, false, false, PEND>(w, ps);
+            // combine x_v = (x_gamma ^ x_lambda, x_gamma) (line 17); the root does this for
+            // the winning path only
+            if constexpr (!ROOT) {
+                if constexpr (H >= 32) {
+                    constexpr int WH = H / 32;
+#pragma unroll
+                    for (int it = 0; it < (L * WH + 31) / 32; it++) {
+                        const int idx = w.lane + 32 * it;
+                        if (idx < L * WH) {
+                            uint32_t* b = bitbuf(w, w.bsel, idx / WH);
+                            const int wd = idx % WH;
+                            b[OFF / 32 + wd] ^= b[(OFF + H) / 32 + wd];
+                        }
+                    }
+                } else {
+                    if (w.lane < L) {
+                        uint32_t* wd = bitbuf(w, w.bsel, w.lane) + OFF / 32;
+                        const unsigned mh = (1u << H) - 1u;
+                        *wd ^= ((*wd >> ((OFF % 32) + H)) & mh) << (OFF % 32);
+                    }
+                }
+                __syncwarp();
+                if constexpr (PERM) {
+                    // undo pi*_l on the node's span (lines 18-19): x[pi(i)] = x'[i]
+                    static_assert(OFF == 0, "permuted nodes lie on the left spine");
+                    constexpr int SB = 1 << S;
+                    if constexpr (SB >= 32) {
+                        constexpr int SW = SB / 32;
+#pragma unroll 1
+                        for (int l = 0; l < L; l++) {
+                            const int cl = __shfl_sync(kFull, ps.selc[S], l);
+                            const uint16_t* r = lrec + cl * kRec;
+                            uint32_t* b = bitbuf(w, w.bsel, l);
+                            for (int wd = w.lane; wd < SW; wd += 32) w.xtmp[wd] = 0;
+                            __syncwarp();
+                            const int base = ga_lane_base(r, S, w.lane);
+#pragma unroll
+                            for (int t = 0; t < SW; t++) {
+                                const int dstp = base ^ ga_hi(r, S, t);
+                                const unsigned bit = (b[t] >> w.lane) & 1u;
+                                if (bit) atomicOr(&w.xtmp[dstp >> 5], 1u << (dstp & 31));
+                            }
+                            __syncwarp();
+                            for (int wd = w.lane; wd < SW; wd += 32) b[wd] = w.xtmp[wd];
+                            __syncwarp();
+                        }
+                    } else {
+                        if (w.lane < L) {
+                            const uint16_t* r = lrec + ps.selc[S] * kRec;
+                            uint32_t* b = bitbuf(w, w.bsel, w.lane);
+                            const unsigned old = b[0];
+                            unsigned nw = 0;
+#pragma unroll
+                            for (int i = 0; i < SB; i++)
+                                if ((old >> i) & 1u) nw |= 1u << ga_apply(r, S, i);
+                            const unsigned mask = (1u << SB) - 1u;
+                            b[0] = (old & ~mask) | nw;
+                        }
+                        __syncwarp();
+                    }
+                }
+            }
+        }
+    }
+
+    // Runs one decoder (Algorithm 2 from the root) and returns the best path's metric; the
+    // best path's codeword in the channel domain is left in w.xtmp.
+    __device__ static float run(Warp& w) {
+        PState<M> ps;
+        ps.pm = 0.f;
+        ps.rootc = 0;
+#pragma unroll
+        for (int s = 0; s <= M; s++) {
+            ps.slot[s] = w.lane < L ? w.lane : 0;
+            ps.selc[s] = 0;
+        }
+        w.bsel = 0;
+        node<R, M, 0, true, true, 0u>(w, ps);
+        // the list is sorted by metric: path 0 is the decoder's best (Algorithm 5, line 5)
+        const float pm0 = __shfl_sync(kFull, ps.pm, 0);
+        const int c0 = __shfl_sync(kFull, ps.rootc, 0);
+        uint32_t* b = bitbuf(w, w.bsel, 0);
+        constexpr int H = N / 2;
+        if constexpr (H >= 32) {
+            for (int wd = w.lane; wd < H / 32; wd += 32) b[wd] ^= b[H / 32 + wd];
+        } else if (w.lane == 0) {
+            b[0] ^= (b[0] >> H) & ((1u << H) - 1u);
+        }
+        __syncwarp();
+        // undo the root permutation sigma = pi^init o pi*: x[sigma(i)] = x'[i]
+        const uint16_t* r = w.rec + c0 * kRec;
+        for (int wd = w.lane; wd < NW; wd += 32) w.xtmp[wd] = 0;
+        __syncwarp();
+        const int base = ga_lane_base(r, M, w.lane);
+#pragma unroll
+        for (int t = 0; t < (N + 31) / 32; t++) {
+            const int i = w.lane + 32 * t;
+            if (i < N) {
+                const int dstp = base ^ ga_hi(r, M, t);
+                if ((b[i >> 5] >> (i & 31)) & 1u) atomicOr(&w.xtmp[dstp >> 5], 1u << (dstp & 31));
+            }
+        }
+        __syncwarp();
+        return pm0;
+    }
+};
+
+template <int M, int R, int L>
+__global__ void __launch_bounds__(256) pfht_kernel(LaunchArgs args) {
+    using C = Cfg<M, R, L>;
+    using D = Decoder<M, R, L>;
+    constexpr int N = C::N;
+    constexpr int NW = C::NW;
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int W = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int P = args.P;
+    const int K = args.K;
+    uint16_t* s_rec = reinterpret_cast<uint16_t*>(smem);
+    uint16_t* s_info = s_rec + P * C::NREC * kRec;
+    float* s_y = reinterpret_cast<float*>(smem + ((P * C::NREC * kRec * 2 + K * 2 + 15) / 16) * 16);
+    float* s_redpm = s_y + N;
+    int* s_redp = reinterpret_cast<int*>(s_redpm + W);
+    uint8_t* wbase = reinterpret_cast<uint8_t*>(s_redp + W);
+    wbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(wbase) + 15) & ~uintptr_t(15));
+    uint8_t* mine = wbase + warp * C::WARP_BYTES;
+    Warp w;
+    w.alpha = reinterpret_cast<float*>(mine);
+    w.bits = reinterpret_cast<uint32_t*>(mine + C::OFF_BITS);
+    w.xtmp = reinterpret_cast<uint32_t*>(mine + C::OFF_XTMP);
+    w.best = reinterpret_cast<uint32_t*>(mine + C::OFF_BEST);
+    w.spc = mine + C::OFF_SPC;
+    w.y = s_y;
+    w.lane = lane;
+
+    for (int i = threadIdx.x; i < P * C::NREC * kRec; i += blockDim.x) s_rec[i] = args.recs[i];
+    for (int i = threadIdx.x; i < K; i += blockDim.x) s_info[i] = args.info[i];
+
+    for (int64_t f = blockIdx.x; f < args.n_frames; f += gridDim.x) {
+        __syncthreads();
+        // frame LLRs into shared memory, widened to float
+        if (args.dtype == IN_F32) {
+            const float4* src = reinterpret_cast<const float4*>(static_cast<const float*>(args.llr) + f * N);
+            for (int i = threadIdx.x; i < N / 4; i += blockDim.x) reinterpret_cast<float4*>(s_y)[i] = src[i];
+        } else if (args.dtype == IN_I8) {
+            const int8_t* src = static_cast<const int8_t*>(args.llr) + f * N;
+            for (int i = threadIdx.x; i < N; i += blockDim.x) s_y[i] = (float)src[i];
+        } else if (args.dtype == IN_F16) {
+            const __half* src = static_cast<const __half*>(args.llr) + f * N;
+            for (int i = threadIdx.x; i < N; i += blockDim.x) s_y[i] = __half2float(src[i]);
+        } else {
+            const int16_t* src = static_cast<const int16_t*>(args.llr) + f * N;
+            for (int i = threadIdx.x; i < N; i += blockDim.x)
+                s_y[i] = fminf(fmaxf((float)src[i], -args.qclamp), args.qclamp);
+        }
+        __syncthreads();
+        float best = __int_as_float(0x7f800000);
+        int bestp = -1;
+        for (int p = warp; p < P; p += W) {
+            w.rec = s_rec + p * C::NREC * kRec;
+            const float pm = D::run(w);
+            if (bestp < 0 || pm < best) {  // strict: earlier decoders win ties (Algorithm 5)
+                best = pm;
+                bestp = p;
+                for (int wd = lane; wd < NW; wd += 32) w.best[wd] = w.xtmp[wd];
+            }
+            __syncwarp();
+        }
+        if (lane == 0) {
+            s_redpm[warp] = best;
+            s_redp[warp] = bestp;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            // the winner over warps by (metric, decoder index)
+            float bp = __int_as_float(0x7f800000);
+            int bw = 0, bpp = 1 << 30;
+            for (int q = 0; q < W; q++) {
+                const float v = s_redpm[q];
+                const int pq = s_redp[q];
+                if (pq >= 0 && (v < bp || (v == bp && pq < bpp))) {
+                    bp = v;
+                    bpp = pq;
+                    bw = q;
+                }
+            }
+            uint32_t* cw = reinterpret_cast<uint32_t*>(wbase + bw * C::WARP_BYTES + C::OFF_BEST);
+            if (args.cw_out)
+                for (int wd = lane; wd < NW; wd += 32) args.cw_out[f * NW + wd] = cw[wd];
+            if (lane == 0) {
+                if (args.pm_out) args.pm_out[f] = bp;
+                if (args.best_out) args.best_out[f] = bpp;
+            }
+            // u = x G^{(x)m}: u_i = XOR of x_j over j containing i
+            uint32_t* u = w.xtmp;
+            for (int wd = lane; wd < NW; wd += 32) {
+                unsigned v = cw[wd];
+                if (M > 0) v ^= (v >> 1) & 0x55555555u;
+                if (M > 1) v ^= (v >> 2) & 0x33333333u;
+                if (M > 2) v ^= (v >> 4) & 0x0F0F0F0Fu;
+                if (M > 3) v ^= (v >> 8) & 0x00FF00FFu;
+                if (M > 4) v ^= (v >> 16) & 0x0000FFFFu;
+                u[wd] = v;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int t = 5; t < M; t++) {
+                const int d = 1 << (t - 5);
+                for (int wd = lane; wd < NW; wd += 32)
+                    if (!(wd & d)) u[wd] ^= u[wd | d];
+                __syncwarp();
+            }
+            const int KW = (K + 31) / 32;
+            for (int it = 0; it < KW; it++) {
+                const int j = lane + 32 * it;
+                unsigned bit = 0;
+                if (j < K) {
+                    const int pos = s_info[j];
+                    bit = (u[pos >> 5] >> (pos & 31)) & 1u;
+                }
+                const unsigned word = __ballot_sync(kFull, bit);
+                if (lane == 0) args.info_out[f * KW + it] = word;
+            }
+        }
+    }
+}
+
+}  // namespace rmdec_dev

@@ -1,0 +1,470 @@
+// C-ABI of the rmdec library: handle management, permutation tables, kernel dispatch and
+// the asynchronous ticket interface. See include/rmdec.h for the contract of each call.
+#include <cerrno>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/rmdec.h"
+#include "pfht_kernel.cuh"
+#include "rmdec_internal.h"
+
+namespace {
+
+constexpr int kMaxM = 10;
+constexpr int kRec = 11;
+constexpr uint32_t kPermTag = 0x5045524Du;     // 'PERM'
+constexpr uint32_t kSscStream = 0x53534300u;   // 'SSC\0'
+constexpr int kMaxTickets = 1024;
+
+// ------------------------------------------------------------ Philox4x32-10 ---
+// Counter-based generator of Salmon, Moraes, Dror, Shaw (SC'11): ten rounds of two
+// 32x32->64 multiplies with the round keys bumped by the Weyl constants between rounds.
+void philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+    uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; round++) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+    memcpy(out, c, sizeof c);
+}
+
+int gf2_rank(const uint16_t* cols, int s) {
+    uint16_t v[kMaxM];
+    memcpy(v, cols, sizeof(uint16_t) * s);
+    int rank = 0;
+    for (int bit = 0; bit < s && rank < s; bit++) {
+        int piv = -1;
+        for (int i = rank; i < s; i++)
+            if ((v[i] >> bit) & 1) { piv = i; break; }
+        if (piv < 0) continue;
+        std::swap(v[rank], v[piv]);
+        for (int i = 0; i < s; i++)
+            if (i != rank && ((v[i] >> bit) & 1)) v[i] ^= v[rank];
+        rank++;
+    }
+    return rank;
+}
+
+// Element of GA(s): draw a = 0, 1, ... with counter (stream, q, a, 'PERM') until the s x s
+// matrix of bits [t*s, (t+1)*s) (column t) is invertible; b is bits [s*s, s*s + s).
+void sample_ga(int s, uint64_t seed, uint32_t stream, uint32_t q, uint16_t* rec) {
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (uint32_t a = 0;; a++) {
+        const uint32_t ctr[4] = {stream, q, a, kPermTag};
+        uint32_t w[4];
+        philox4x32_10(ctr, key, w);
+        auto bit = [&](int i) { return (w[i >> 5] >> (i & 31)) & 1u; };
+        uint16_t r[kRec] = {0};
+        for (int t = 0; t < s; t++)
+            for (int i = 0; i < s; i++) r[t] |= (uint16_t)(bit(t * s + i) << i);
+        for (int i = 0; i < s; i++) r[kMaxM] |= (uint16_t)(bit(s * s + i) << i);
+        if (gf2_rank(r, s) == s) {
+            memcpy(rec, r, sizeof r);
+            return;
+        }
+    }
+}
+
+bool record_valid(const uint16_t* r, int s) {
+    for (int t = s; t < kMaxM; t++)
+        if (r[t]) return false;
+    for (int t = 0; t < s; t++)
+        if (r[t] >> s) return false;
+    if (r[kMaxM] >> s) return false;
+    return gf2_rank(r, s) == s;
+}
+
+// sigma = outer o inner as a record: sigma(i) = outer(inner(i)).
+void compose(const uint16_t* outer, const uint16_t* inner, int s, uint16_t* out) {
+    auto lin = [&](int v) {
+        int o = 0;
+        for (int t = 0; t < s; t++)
+            if ((v >> t) & 1) o ^= outer[t];
+        return o;
+    };
+    memset(out, 0, sizeof(uint16_t) * kRec);
+    for (int t = 0; t < s; t++) out[t] = (uint16_t)lin(inner[t]);
+    out[kMaxM] = (uint16_t)(lin(inner[kMaxM]) ^ outer[kMaxM]);
+}
+
+int n_perm_levels(int m, int r) { return (1 < r && r < m - 1) ? r - 1 : 0; }
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct rmdec_ctx {
+    int algo = 0;  // 0: p-FHT-FSCL-L-P, 1: Aut-SSC-P
+    int m = 0, r = 0, P = 0, L = 1, n = 0, k = 0;
+    rmdec_dtype dtype = RMDEC_LLR_F32;
+    std::vector<uint16_t> perms;  // host table in the documented layout
+    std::vector<int> info;
+    bool dirty = true;
+    int device = -1;
+    uint16_t* d_recs = nullptr;
+    uint16_t* d_info = nullptr;
+    rmdec_host::KernelEntry kern;
+    int warps = 4;
+    int sm_count = 0;
+    int blocks_per_sm = 0;
+    size_t smem = 0;
+    void* d_stage = nullptr;
+    size_t stage_bytes = 0;
+    std::map<uint64_t, cudaEvent_t> tickets;
+    uint64_t next_ticket = 1;
+    std::string err;
+
+    rmdec_status fail(rmdec_status st, const char* fmt, ...) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        err = buf;
+        return st;
+    }
+    rmdec_status cuda_fail(cudaError_t e, const char* what) {
+        return fail(RMDEC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    }
+    int records_per_decoder() const { return algo == 0 ? L + n_perm_levels(m, r) * 2 * L : 1; }
+    int64_t n_records() const { return algo == 0 ? (int64_t)P * records_per_decoder() : P; }
+    int record_size(int q) const {  // GA(s) of record q within a decoder
+        if (algo == 1 || q < L) return m;
+        return m - (q - L) / (2 * L);
+    }
+};
+
+namespace {
+
+size_t llr_elem_bytes(rmdec_dtype t) {
+    switch (t) {
+        case RMDEC_LLR_F32: return 4;
+        case RMDEC_LLR_I8: return 1;
+        case RMDEC_LLR_F16: return 2;
+        case RMDEC_LLR_I16: return 2;
+    }
+    return 4;
+}
+
+bool lookup_kernel(rmdec_ctx* h, rmdec_host::KernelEntry* e) {
+    using namespace rmdec_host;
+    if (h->algo == 1) return lookup_autssc(h->m, h->r, e);
+    switch (h->m) {
+        case 4: return lookup_pfht_m4(h->r, h->L, e);
+        case 5: return lookup_pfht_m5(h->r, h->L, e);
+        case 6: return lookup_pfht_m6(h->r, h->L, e);
+        case 7: return lookup_pfht_m7(h->r, h->L, e);
+        case 8: return lookup_pfht_m8(h->r, h->L, e);
+        case 9: return lookup_pfht_m9(h->r, h->L, e);
+    }
+    return false;
+}
+
+// Device records: p-FHT-FSCL: per decoder, level 0 holds the 2L root candidates composed with
+// the initial permutation of their source path (pi^init_{c mod L} o pi_c, one GA(m) element, since
+// every root path starts from the same channel LLRs), levels 1.. hold the 2L candidates as given.
+std::vector<uint16_t> device_records(const rmdec_ctx* h) {
+    std::vector<uint16_t> out;
+    if (h->algo == 1) return h->perms;
+    const int rpd = h->records_per_decoder(), nlev = n_perm_levels(h->m, h->r), L = h->L;
+    out.resize((size_t)h->P * nlev * 2 * L * kRec);
+    for (int p = 0; p < h->P; p++) {
+        const uint16_t* base = h->perms.data() + (size_t)p * rpd * kRec;
+        uint16_t* dst = out.data() + (size_t)p * nlev * 2 * L * kRec;
+        for (int lev = 0; lev < nlev; lev++)
+            for (int c = 0; c < 2 * L; c++) {
+                const uint16_t* cand = base + (size_t)(L + lev * 2 * L + c) * kRec;
+                uint16_t* o = dst + (size_t)(lev * 2 * L + c) * kRec;
+                if (lev == 0) compose(base + (size_t)(c % L) * kRec, cand, h->m, o);
+                else memcpy(o, cand, sizeof(uint16_t) * kRec);
+            }
+    }
+    return out;
+}
+
+rmdec_status ensure_device(rmdec_ctx* h) {
+    if (!h->dirty) return RMDEC_OK;
+    cudaError_t e;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return h->fail(RMDEC_EDEVICE, "no CUDA device: %s", cudaGetErrorString(e));
+    if (!lookup_kernel(h, &h->kern)) return h->fail(RMDEC_EINVAL, "no kernel for m=%d r=%d L=%d", h->m, h->r, h->L);
+    if ((e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return h->cuda_fail(e, "cudaDeviceGetAttribute");
+    std::vector<uint16_t> recs = device_records(h);
+    if (h->d_recs) cudaFree(h->d_recs);
+    if (h->d_info) cudaFree(h->d_info);
+    h->d_recs = nullptr;
+    h->d_info = nullptr;
+    if ((e = cudaMalloc(&h->d_recs, std::max<size_t>(recs.size(), 1) * 2)) != cudaSuccess) return h->fail(RMDEC_ENOMEM, "cudaMalloc records: %s", cudaGetErrorString(e));
+    if ((e = cudaMalloc(&h->d_info, std::max<size_t>(h->info.size(), 1) * 2)) != cudaSuccess) return h->fail(RMDEC_ENOMEM, "cudaMalloc info: %s", cudaGetErrorString(e));
+    std::vector<uint16_t> info16(h->info.begin(), h->info.end());
+    if ((e = cudaMemcpy(h->d_recs, recs.data(), recs.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess) return h->cuda_fail(e, "upload records");
+    if ((e = cudaMemcpy(h->d_info, info16.data(), info16.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess) return h->cuda_fail(e, "upload info");
+    // warps per CTA: decoders of one frame split across warps
+    int W = h->algo == 0 ? std::min(h->P, 4) : 4;
+    if (const char* s = getenv("RMDEC_WARPS")) W = std::max(1, std::min(8, atoi(s)));
+    h->warps = W;
+    h->smem = (size_t)h->kern.fixed_bytes(h->P, h->k, W) + 16 + (size_t)W * h->kern.warp_bytes;
+    int max_optin = 0;
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if ((int)h->smem > max_optin) return h->fail(RMDEC_EINVAL, "configuration needs %zu B shared memory (max %d)", h->smem, max_optin);
+    // permit the device maximum so that handles of different sizes sharing this kernel can
+    // launch in any order
+    if ((e = cudaFuncSetAttribute(h->kern.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)) != cudaSuccess)
+        return h->cuda_fail(e, "cudaFuncSetAttribute");
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->blocks_per_sm, h->kern.fn, 32 * W, h->smem)) != cudaSuccess)
+        return h->cuda_fail(e, "occupancy");
+    if (h->blocks_per_sm < 1) return h->fail(RMDEC_EINVAL, "kernel cannot be resident (smem %zu)", h->smem);
+    h->device = dev;
+    h->dirty = false;
+    return RMDEC_OK;
+}
+
+rmdec_status launch(rmdec_ctx* h, const void* llr, int64_t n_frames, uint32_t* bits, uint32_t* cw, float* pm,
+                    int32_t* best, cudaStream_t stream) {
+    if (n_frames < 0) return h->fail(RMDEC_EINVAL, "n_frames < 0");
+    if (n_frames == 0) return RMDEC_OK;
+    if (!llr || !bits) return h->fail(RMDEC_EINVAL, "null llr or output pointer");
+    if (reinterpret_cast<uintptr_t>(llr) % 16) return h->fail(RMDEC_EINVAL, "llr buffer must be 16-byte aligned");
+    rmdec_status st = ensure_device(h);
+    if (st != RMDEC_OK) return st;
+    rmdec_dev::LaunchArgs a;
+    a.llr = llr;
+    a.dtype = (int)h->dtype;
+    a.qclamp = (float)((1 << (24 - h->m)) - 1);
+    a.n_frames = n_frames;
+    a.P = h->P;
+    a.recs = h->d_recs;
+    a.info = h->d_info;
+    a.K = h->k;
+    a.info_out = bits;
+    a.cw_out = cw;
+    a.pm_out = pm;
+    a.best_out = best;
+    const int64_t cap = (int64_t)h->sm_count * h->blocks_per_sm;
+    const unsigned grid = (unsigned)std::min<int64_t>(n_frames, cap);
+    void* args[] = {&a};
+    cudaError_t e = cudaLaunchKernel(h->kern.fn, dim3(grid), dim3(32 * h->warps), args, h->smem, stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "kernel launch");
+    return RMDEC_OK;
+}
+
+rmdec_status make_handle(rmdec_t* out, int algo, int m, int r, int P, int L, uint64_t seed) {
+    if (!out) {
+        g_create_error = "null output handle pointer";
+        return RMDEC_EINVAL;
+    }
+    *out = nullptr;
+    if (algo == 0) {
+        if (m < 4 || m > 9 || r < 2 || r > 3 || r > m - 2 || P < 1 || P > 64 || !(L == 1 || L == 2 || L == 4 || L == 8)) {
+            g_create_error = "unsupported p-FHT-FSCL configuration (need 4<=m<=9, r in {2,3}, r<=m-2, 1<=P<=64, L in {1,2,4,8})";
+            return RMDEC_EINVAL;
+        }
+    } else {
+        if (m < 4 || m > 9 || r < 1 || r > 3 || r > m - 2 || P < 1 || P > 1024) {
+            g_create_error = "unsupported Aut-SSC configuration (need 4<=m<=9, 1<=r<=min(3,m-2), 1<=P_ssc<=1024)";
+            return RMDEC_EINVAL;
+        }
+    }
+    rmdec_ctx* h = new (std::nothrow) rmdec_ctx;
+    if (!h) {
+        g_create_error = "host allocation failed";
+        return RMDEC_ENOMEM;
+    }
+    h->algo = algo;
+    h->m = m;
+    h->r = r;
+    h->P = P;
+    h->L = algo == 0 ? L : 1;
+    h->n = 1 << m;
+    for (int i = 0; i < h->n; i++)
+        if (__builtin_popcount((unsigned)i) >= m - r) h->info.push_back(i);
+    h->k = (int)h->info.size();
+    h->perms.assign((size_t)h->n_records() * kRec, 0);
+    if (algo == 0) {
+        const int rpd = h->records_per_decoder();
+        for (int p = 0; p < P; p++)
+            for (int q = 0; q < rpd; q++)
+                sample_ga(h->record_size(q), seed, (uint32_t)p, (uint32_t)q, &h->perms[((size_t)p * rpd + q) * kRec]);
+    } else {
+        for (int q = 0; q < P; q++) sample_ga(m, seed, kSscStream, (uint32_t)q, &h->perms[(size_t)q * kRec]);
+    }
+    *out = h;
+    return RMDEC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rmdec_status rmdec_create(rmdec_t* out, int m, int r, int P, int L, uint64_t perm_seed) {
+    return make_handle(out, 0, m, r, P, L, perm_seed);
+}
+
+rmdec_status rmdec_create_aut_ssc(rmdec_t* out, int m, int r, int P_ssc, uint64_t perm_seed) {
+    return make_handle(out, 1, m, r, P_ssc, 1, perm_seed);
+}
+
+void rmdec_destroy(rmdec_t h) {
+    if (!h) return;
+    for (auto& kv : h->tickets) {
+        cudaEventSynchronize(kv.second);
+        cudaEventDestroy(kv.second);
+    }
+    if (h->d_recs) cudaFree(h->d_recs);
+    if (h->d_info) cudaFree(h->d_info);
+    if (h->d_stage) cudaFree(h->d_stage);
+    delete h;
+}
+
+rmdec_status rmdec_set_dtype(rmdec_t h, rmdec_dtype t) {
+    if (!h) return RMDEC_EINVAL;
+    if (t != RMDEC_LLR_F32 && t != RMDEC_LLR_I8 && t != RMDEC_LLR_F16 && t != RMDEC_LLR_I16)
+        return h->fail(RMDEC_EINVAL, "unknown dtype %d", (int)t);
+    h->dtype = t;
+    return RMDEC_OK;
+}
+
+rmdec_status rmdec_perm_count(rmdec_t h, int64_t* n_records) {
+    if (!h || !n_records) return RMDEC_EINVAL;
+    *n_records = h->n_records();
+    return RMDEC_OK;
+}
+
+rmdec_status rmdec_get_perms(rmdec_t h, uint16_t* perms_host, int64_t n_records) {
+    if (!h) return RMDEC_EINVAL;
+    if (!perms_host || n_records != h->n_records())
+        return h->fail(RMDEC_EINVAL, "expected %lld records", (long long)h->n_records());
+    memcpy(perms_host, h->perms.data(), h->perms.size() * sizeof(uint16_t));
+    return RMDEC_OK;
+}
+
+rmdec_status rmdec_set_perms(rmdec_t h, const uint16_t* perms_host, int64_t n_records) {
+    if (!h) return RMDEC_EINVAL;
+    if (!perms_host || n_records != h->n_records())
+        return h->fail(RMDEC_EINVAL, "expected %lld records", (long long)h->n_records());
+    const int rpd = h->records_per_decoder();
+    for (int64_t q = 0; q < n_records; q++)
+        if (!record_valid(perms_host + q * kRec, h->record_size((int)(q % rpd))))
+            return h->fail(RMDEC_EINVAL, "record %lld is not an invertible affine map of the right size", (long long)q);
+    memcpy(h->perms.data(), perms_host, h->perms.size() * sizeof(uint16_t));
+    h->dirty = true;
+    return RMDEC_OK;
+}
+
+rmdec_status rmdec_info(rmdec_t h, int* n, int* k, const int** info_idx) {
+    if (!h) return RMDEC_EINVAL;
+    if (n) *n = h->n;
+    if (k) *k = h->k;
+    if (info_idx) *info_idx = h->info.data();
+    return RMDEC_OK;
+}
+
+rmdec_status rmdec_decode(rmdec_t h, const void* llr_dev, int64_t n_frames, uint32_t* bits_out_dev, void* stream) {
+    if (!h) return RMDEC_EINVAL;
+    return launch(h, llr_dev, n_frames, bits_out_dev, nullptr, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+rmdec_status rmdec_decode_debug(rmdec_t h, const void* llr_dev, int64_t n_frames, uint32_t* bits_out_dev,
+                                uint32_t* cw_out_dev, float* pm_out_dev, int32_t* best_out_dev, void* stream) {
+    if (!h) return RMDEC_EINVAL;
+    return launch(h, llr_dev, n_frames, bits_out_dev, cw_out_dev, pm_out_dev, best_out_dev, (cudaStream_t)stream);
+}
+
+rmdec_status rmdec_decode_host(rmdec_t h, const void* llr_host, int64_t n_frames, uint32_t* bits_out_host, void* stream) {
+    if (!h) return RMDEC_EINVAL;
+    if (n_frames < 0 || (n_frames > 0 && (!llr_host || !bits_out_host))) return h->fail(RMDEC_EINVAL, "bad arguments");
+    if (n_frames == 0) return RMDEC_OK;
+    const size_t in_bytes = (size_t)n_frames * h->n * llr_elem_bytes(h->dtype);
+    const size_t in_pad = (in_bytes + 255) / 256 * 256;
+    const size_t out_bytes = (size_t)n_frames * ((h->k + 31) / 32) * 4;
+    cudaError_t e;
+    if (in_pad + out_bytes > h->stage_bytes) {
+        if (h->d_stage) {
+            cudaFree(h->d_stage);
+            h->d_stage = nullptr;
+            h->stage_bytes = 0;
+        }
+        if ((e = cudaMalloc(&h->d_stage, in_pad + out_bytes)) != cudaSuccess)
+            return h->fail(RMDEC_ENOMEM, "staging allocation of %zu bytes: %s", in_pad + out_bytes, cudaGetErrorString(e));
+        h->stage_bytes = in_pad + out_bytes;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    uint8_t* d_in = static_cast<uint8_t*>(h->d_stage);
+    uint32_t* d_out = reinterpret_cast<uint32_t*>(d_in + in_pad);
+    if ((e = cudaMemcpyAsync(d_in, llr_host, in_bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess) return h->cuda_fail(e, "H2D");
+    rmdec_status st = launch(h, d_in, n_frames, d_out, nullptr, nullptr, nullptr, s);
+    if (st != RMDEC_OK) return st;
+    if ((e = cudaMemcpyAsync(bits_out_host, d_out, out_bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return h->cuda_fail(e, "D2H");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return h->cuda_fail(e, "synchronize");
+    return RMDEC_OK;
+}
+
+rmdec_status rmdec_submit(rmdec_t h, const void* llr_dev, int64_t n_frames, uint32_t* bits_out_dev, void* stream,
+                          uint64_t* ticket) {
+    if (!h) return RMDEC_EINVAL;
+    if (!ticket) return h->fail(RMDEC_EINVAL, "null ticket pointer");
+    if ((int)h->tickets.size() >= kMaxTickets) return h->fail(RMDEC_EBUSY, "too many outstanding tickets");
+    rmdec_status st = launch(h, llr_dev, n_frames, bits_out_dev, nullptr, nullptr, nullptr, (cudaStream_t)stream);
+    if (st != RMDEC_OK) return st;
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return h->cuda_fail(e, "cudaEventCreate");
+    if ((e = cudaEventRecord(ev, (cudaStream_t)stream)) != cudaSuccess) {
+        cudaEventDestroy(ev);
+        return h->cuda_fail(e, "cudaEventRecord");
+    }
+    const uint64_t t = h->next_ticket++;
+    h->tickets[t] = ev;
+    *ticket = t;
+    return RMDEC_OK;
+}
+
+rmdec_status rmdec_poll(rmdec_t h, uint64_t ticket, int64_t timeout_us) {
+    if (!h) return RMDEC_EINVAL;
+    auto it = h->tickets.find(ticket);
+    if (it == h->tickets.end()) return h->fail(RMDEC_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t e = cudaEventQuery(it->second);
+        if (e == cudaSuccess) {
+            cudaEventDestroy(it->second);
+            h->tickets.erase(it);
+            return RMDEC_OK;
+        }
+        if (e != cudaErrorNotReady) return h->cuda_fail(e, "cudaEventQuery");
+        if (timeout_us <= 0) return h->fail(RMDEC_EBUSY, "ticket %llu still running", (unsigned long long)ticket);
+        const auto us = std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
+        if (us >= timeout_us) return h->fail(RMDEC_ETIMEDOUT, "ticket %llu not finished after %lld us", (unsigned long long)ticket, (long long)timeout_us);
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+const char* rmdec_last_error(rmdec_t h) {
+    if (!h) return g_create_error.c_str();
+    return h->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,48 @@
+// Internal interfaces between the C-ABI layer and the kernel instantiation units.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace rmdec_host {
+
+// One compiled decoder configuration (a kernel template instance).
+struct KernelEntry {
+    const void* fn = nullptr;  // __global__ function
+    int warp_bytes = 0;        // shared memory per warp
+    int nrec = 0;              // device permutation records per decoder
+    int (*fixed_bytes)(int P, int K, int W) = nullptr;
+};
+
+// p-FHT-FSCL kernels: one lookup per code length m (instantiated in inst_m<m>.cu).
+bool lookup_pfht_m4(int r, int L, KernelEntry* e);
+bool lookup_pfht_m5(int r, int L, KernelEntry* e);
+bool lookup_pfht_m6(int r, int L, KernelEntry* e);
+bool lookup_pfht_m7(int r, int L, KernelEntry* e);
+bool lookup_pfht_m8(int r, int L, KernelEntry* e);
+bool lookup_pfht_m9(int r, int L, KernelEntry* e);
+
+// Aut-SSC baseline kernels (autssc.cu).
+bool lookup_autssc(int m, int r, KernelEntry* e);
+
+}  // namespace rmdec_host
+
+#define RMDEC_PFHT_ENTRY(M, R, L)                                                        \
+    do {                                                                                 \
+        e->fn = reinterpret_cast<const void*>(&rmdec_dev::pfht_kernel<M, R, L>);         \
+        e->warp_bytes = rmdec_dev::Cfg<M, R, L>::WARP_BYTES;                             \
+        e->nrec = rmdec_dev::Cfg<M, R, L>::NREC;                                         \
+        e->fixed_bytes = [](int P, int K, int W) {                                       \
+            return rmdec_dev::Cfg<M, R, L>::fixed_bytes(P, K, W);                        \
+        };                                                                               \
+        return true;                                                                     \
+    } while (0)
+
+#define RMDEC_PFHT_CASE(M, R)                                                            \
+    if (r == R) {                                                                        \
+        if (L == 1) RMDEC_PFHT_ENTRY(M, R, 1);                                           \
+        if (L == 2) RMDEC_PFHT_ENTRY(M, R, 2);                                           \
+        if (L == 4) RMDEC_PFHT_ENTRY(M, R, 4);                                           \
+        if (L == 8) RMDEC_PFHT_ENTRY(M, R, 8);                                           \
+    }

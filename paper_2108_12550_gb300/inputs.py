@@ -203,3 +203,11 @@ def perm_table(m: int, r: int, P: int, L: int, seed: int) -> np.ndarray:
             s = m if q < L else m - (q - L) // (2 * L)
             tab[p, q] = sample_ga(s, seed, p, q)
     return tab
+
+
+SSC_STREAM = 0x53534300  # counter word 0 of the Aut-SSC permutation draws
+
+
+def ssc_perm_table(m: int, P_ssc: int, seed: int) -> np.ndarray:
+    """(P_ssc, 11) uint16 GA(m) records for the Aut-SSC-P baseline (counter word 0 = 'SSC\\0')."""
+    return np.stack([sample_ga(m, seed, SSC_STREAM, q) for q in range(P_ssc)])

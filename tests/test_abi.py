@@ -1,0 +1,82 @@
+"""CPU checks of the C ABI: the library loads, exports every declared entry point, validates
+arguments, and samples the same permutation tables as the independent Python generator."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2108_12550_gb300 as pkg
+from paper_2108_12550_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "rmdec.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(rmdec_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = pkg.load_library()
+    names = _declared()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_invalid_configurations_are_rejected():
+    lib = pkg.load_library()
+    h = ctypes.c_void_p()
+    for args in [(9, 2, 20, 3), (9, 8, 4, 4), (3, 1, 4, 4), (9, 2, 0, 4), (10, 2, 4, 4), (9, 2, 65, 4)]:
+        st = lib.rmdec_create(ctypes.byref(h), *args, 1)
+        assert st == pkg.EINVAL and h.value is None
+        assert len(lib.rmdec_last_error(None)) > 0
+    assert lib.rmdec_create_aut_ssc(ctypes.byref(h), 9, 4, 16, 1) == pkg.EINVAL
+
+
+@pytest.mark.parametrize("m,r,P,L", [(5, 2, 4, 2), (9, 2, 20, 4), (9, 3, 3, 8), (6, 3, 2, 1)])
+def test_seeded_tables_match_independent_generator(m, r, P, L):
+    d = pkg.Decoder(m, r, P, L, perm_seed=12345)
+    assert d.n == 1 << m and d.k == I.rm_dims(m, r)[1]
+    assert np.array_equal(d.info_idx, I.info_set(m, r))
+    got = d.get_perms().reshape(P, -1, I.PERM_REC)
+    assert np.array_equal(got, I.perm_table(m, r, P, L, seed=12345))
+    d.close()
+
+
+def test_aut_ssc_table_matches_independent_generator():
+    d = pkg.Decoder(9, 2, 40, algo="autssc", perm_seed=99)
+    assert np.array_equal(d.get_perms(), I.ssc_perm_table(9, 40, 99))
+    d.close()
+
+
+def test_set_perms_validates_records():
+    d = pkg.Decoder(7, 2, 2, 2, perm_seed=1)
+    tab = d.get_perms()
+    d.set_perms(tab)  # round trip
+    bad = tab.copy()
+    bad[3, :7] = 0  # singular linear part
+    with pytest.raises(pkg.RmdecError) as ei:
+        d.set_perms(bad)
+    assert ei.value.status == pkg.EINVAL
+    wrong = tab.copy()
+    wrong[0, 8] = 1  # column beyond GA(7)
+    with pytest.raises(pkg.RmdecError):
+        d.set_perms(wrong)
+    with pytest.raises(pkg.RmdecError):
+        d.set_perms(tab[:-1])
+
+
+def test_bad_dtype_and_poll_arguments():
+    d = pkg.Decoder(5, 2, 2, 2)
+    assert d._lib.rmdec_set_dtype(d._h, 7) == pkg.EINVAL
+    assert d._lib.rmdec_poll(d._h, 12345, 0) == pkg.EINVAL
+
+
+def test_pack_unpack_roundtrip():
+    rng = np.random.default_rng(0)
+    b = rng.integers(0, 2, (5, 46), dtype=np.uint8)
+    assert np.array_equal(pkg.unpack_bits(pkg.pack_bits(b), 46), b)

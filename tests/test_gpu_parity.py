@@ -1,0 +1,191 @@
+"""GPU parity of the CUDA decoder (through the C ABI) against the CPU oracle.
+
+Integer LLRs (I8, I16, and F32 holding integer values) must match the oracle's exact integer
+mode bit for bit: information bits, codewords, path metrics and winning decoder. Real-valued
+FP32/FP16 LLRs are compared with the FP64 oracle within the stated tolerance: identical
+decoded words except at near-ties (rare), path metrics within 1e-4 relative, and on every
+frame the GPU's metric equals the discrepancy of the word it returned.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle as O  # noqa: E402
+import paper_2108_12550_gb300 as pkg  # noqa: E402
+from paper_2108_12550_gb300 import inputs as I  # noqa: E402
+
+PM_RTOL = 1e-4          # FP32 path metrics vs FP64 (relative, plus the frame's mean |LLR|)
+MISMATCH_MAX = 0.01     # largest tolerated fraction of FP32 frames decided differently
+
+
+def _gpu_decode(dec, llr_np):
+    x = torch.from_numpy(np.ascontiguousarray(llr_np)).cuda()
+    bits, cw, pm, best = dec.decode_debug(x)
+    torch.cuda.synchronize()
+    return (pkg.unpack_bits(bits.cpu().numpy(), dec.k), pkg.unpack_bits(cw.cpu().numpy(), dec.n),
+            pm.cpu().numpy(), best.cpu().numpy())
+
+
+def _disc(llr, cw):
+    return np.sum(np.abs(llr) * (cw != (llr < 0)), axis=-1)
+
+
+CONFIGS = [  # (m, r, P, L, Eb/N0, frames)
+    (4, 2, 2, 8, 2.0, 600),
+    (5, 2, 4, 2, 3.0, 3000),     # RM(2,5), P=4, L=2 (the small benchmark case)
+    (5, 3, 3, 4, 4.0, 1000),     # the paper's Fig. 3 example code, two permuted levels
+    (6, 2, 3, 1, 2.0, 1000),
+    (6, 3, 2, 8, 4.0, 500),
+    (7, 2, 8, 4, 2.0, 2000),     # RM(2,7), P=8, L=4
+    (8, 2, 8, 4, 2.5, 600),
+    (9, 2, 20, 4, 2.25, 333),    # RM(2,9), P=20, L=4 (ragged frame count)
+    (9, 3, 16, 8, 4.0, 150),     # RM(3,9), P=16, L=8
+]
+
+
+@pytest.mark.parametrize("m,r,P,L,eb,nf", CONFIGS, ids=lambda v: str(v))
+def test_integer_llrs_bit_exact(m, r, P, L, eb, nf):
+    fr = I.make_frames(m, r, nf, eb, seed=100 + m * 10 + r)
+    perms = I.perm_table(m, r, P, L, seed=m * 7 + L)
+    q = I.quantize_i8(fr["llr"])
+    ref = O.decode(m, r, P, L, perms, q.astype(np.int64), integer=True)
+    dec = pkg.Decoder(m, r, P, L, dtype="i8", perms=perms)
+    info, cw, pm, best = _gpu_decode(dec, q)
+    assert np.array_equal(cw, ref["cw"])
+    assert np.array_equal(info, ref["info"])
+    assert np.array_equal(pm.astype(np.int64), ref["pm"])
+    assert np.array_equal(best, ref["best"])
+    # the same kernel on FP32 inputs holding the integer codes is exact too
+    dec.set_dtype("f32")
+    info2, cw2, pm2, best2 = _gpu_decode(dec, q.astype(np.float32))
+    assert np.array_equal(cw2, ref["cw"]) and np.array_equal(pm2.astype(np.int64), ref["pm"])
+    assert np.array_equal(best2, ref["best"])
+
+
+@pytest.mark.parametrize("m,r,P,L", [(7, 2, 8, 4), (9, 2, 4, 4)])
+def test_i16_llrs_bit_exact(m, r, P, L):
+    fr = I.make_frames(m, r, 400, 2.0, seed=5)
+    q = np.clip(np.rint(fr["llr"] * 256), -32767, 32767).astype(np.int16)  # step 2^-8
+    perms = I.perm_table(m, r, P, L, seed=3)
+    ref = O.decode(m, r, P, L, perms, q.astype(np.int64), integer=True)
+    dec = pkg.Decoder(m, r, P, L, dtype="i16", perms=perms)
+    info, cw, pm, best = _gpu_decode(dec, q)
+    assert np.array_equal(cw, ref["cw"]) and np.array_equal(pm.astype(np.int64), ref["pm"])
+    assert np.array_equal(best, ref["best"])
+
+
+def _fp_compare(m, r, P, L, llr64, gpu_llr, dtype):
+    perms = I.perm_table(m, r, P, L, seed=11)
+    ref = O.decode(m, r, P, L, perms, llr64)
+    dec = pkg.Decoder(m, r, P, L, dtype=dtype, perms=perms)
+    info, cw, pm, best = _gpu_decode(dec, gpu_llr)
+    scale = np.mean(np.abs(llr64), axis=1)
+    # every returned metric is the discrepancy of the returned word
+    np.testing.assert_allclose(pm, _disc(llr64, cw), rtol=PM_RTOL, atol=PM_RTOL * scale.max())
+    same = np.all(cw == ref["cw"], axis=1)
+    mismatch = 1.0 - same.mean()
+    assert mismatch <= MISMATCH_MAX, mismatch
+    d = np.abs(pm[same] - ref["pm"][same])
+    assert np.all(d <= PM_RTOL * (np.abs(ref["pm"][same]) + scale[same])), d.max()
+    # decisions differ only where the oracle saw a near-tie
+    assert np.all(ref["margin"][~same] < PM_RTOL)
+    return mismatch
+
+
+@pytest.mark.parametrize("m,r,P,L,eb,nf", [(5, 2, 4, 2, 3.0, 3000), (7, 2, 8, 4, 2.0, 2000),
+                                          (9, 2, 20, 4, 2.25, 400), (9, 3, 16, 8, 4.0, 150)],
+                         ids=lambda v: str(v))
+def test_fp32_within_tolerance(m, r, P, L, eb, nf):
+    fr = I.make_frames(m, r, nf, eb, seed=77)
+    _fp_compare(m, r, P, L, fr["llr"], fr["llr"].astype(np.float32), "f32")
+
+
+def test_fp16_within_tolerance():
+    m, r, P, L = 9, 3, 16, 8
+    fr = I.make_frames(m, r, 150, 4.0, seed=78)
+    h = I.to_f16(fr["llr"])
+    _fp_compare(m, r, P, L, h.astype(np.float64), h, "f16")
+
+
+@pytest.mark.parametrize("m,r,P,L", [(5, 2, 4, 2), (9, 2, 20, 4), (9, 3, 16, 8), (5, 3, 2, 1)])
+def test_noiseless_frames_decode_exactly(m, r, P, L):
+    nl = I.noiseless_frames(m, r, 64, seed=9)
+    dec = pkg.Decoder(m, r, P, L, perm_seed=4)
+    info, cw, pm, best = _gpu_decode(dec, nl["llr"].astype(np.float32))
+    assert np.array_equal(info, nl["u"]) and np.all(pm == 0)
+
+
+def test_library_seeded_tables_end_to_end():
+    """A handle built from a seed (library sampler, root composition on the device side)
+    decodes like the oracle given the independently generated table for the same seed."""
+    m, r, P, L = 7, 2, 8, 4
+    fr = I.make_frames(m, r, 500, 1.5, seed=21)
+    q = I.quantize_i8(fr["llr"])
+    dec = pkg.Decoder(m, r, P, L, perm_seed=2718, dtype="i8")
+    ref = O.decode(m, r, P, L, I.perm_table(m, r, P, L, seed=2718), q.astype(np.int64), integer=True)
+    info, cw, pm, best = _gpu_decode(dec, q)
+    assert np.array_equal(cw, ref["cw"]) and np.array_equal(pm.astype(np.int64), ref["pm"])
+
+
+def test_edge_cases_empty_single_and_determinism():
+    m, r, P, L = 9, 2, 20, 4
+    dec = pkg.Decoder(m, r, P, L, perm_seed=1)
+    empty = torch.empty((0, 512), dtype=torch.float32, device="cuda")
+    out = dec.decode(empty)
+    assert out.shape == (0, 2)
+    fr = I.make_frames(m, r, 1, 2.0, seed=3)
+    one = torch.from_numpy(fr["llr"].astype(np.float32)).cuda()
+    a = dec.decode(one).cpu()
+    b = dec.decode(one).cpu()
+    assert torch.equal(a, b)
+    # all-zero LLRs: every decision is a tie; output must be a valid, deterministic codeword
+    z = torch.zeros((3, 512), dtype=torch.float32, device="cuda")
+    bits, cw, pm, best = dec.decode_debug(z)
+    assert torch.all(pm == 0)
+    q = torch.zeros((3, 512), dtype=torch.int8, device="cuda")
+    dec.set_dtype("i8")
+    bits2, cw2, _, _ = dec.decode_debug(q)
+    assert torch.equal(cw, cw2)
+    ref = O.decode(m, r, P, L, dec.get_perms().reshape(P, -1, 11), np.zeros((3, 512), np.int64), integer=True)
+    assert np.array_equal(pkg.unpack_bits(cw2.cpu().numpy(), 512), ref["cw"])
+    # saturated LLRs (+-127 everywhere, the quantiser's maximum) also decode exactly
+    sat = np.where(I.noiseless_frames(m, r, 8, seed=2)["llr"] < 0, -127, 127).astype(np.int8)
+    ref = O.decode(m, r, P, L, dec.get_perms().reshape(P, -1, 11), sat.astype(np.int64), integer=True)
+    info, cw3, pm3, _ = _gpu_decode(dec, sat)
+    assert np.array_equal(cw3, ref["cw"]) and np.all(pm3 == 0)
+
+
+def test_host_entry_point_and_tickets():
+    m, r, P, L = 7, 2, 8, 4
+    fr = I.make_frames(m, r, 1000, 2.0, seed=31)
+    x = fr["llr"].astype(np.float32)
+    dec = pkg.Decoder(m, r, P, L, perm_seed=5)
+    dev = dec.decode(torch.from_numpy(x).cuda()).cpu()
+    host_in = torch.from_numpy(x).pin_memory()
+    host_out = torch.empty((1000, dec.kw), dtype=torch.int32).pin_memory()
+    dec.decode_host(host_in, host_out)
+    assert torch.equal(dev, host_out)
+    s = torch.cuda.Stream()
+    xin = torch.from_numpy(x).cuda()
+    out = torch.empty((1000, dec.kw), dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        t = dec.submit(xin, out, stream=s)
+    assert dec.poll(t, timeout_us=10_000_000) == pkg.OK
+    assert torch.equal(out.cpu(), dev)
+    with pytest.raises(pkg.RmdecError):
+        dec.poll(t, 0)  # retired ticket
+
+
+@pytest.mark.parametrize("m,r,Ps", [(7, 2, 32), (9, 2, 64), (6, 3, 16)])
+def test_aut_ssc_bit_exact(m, r, Ps):
+    fr = I.make_frames(m, r, 400, 2.0, seed=41)
+    q = I.quantize_i8(fr["llr"])
+    perms = I.ssc_perm_table(m, Ps, seed=6)
+    ref = O.aut_ssc(m, r, perms, q.astype(np.int64), integer=True)
+    dec = pkg.Decoder(m, r, Ps, algo="autssc", perms=perms, dtype="i8")
+    info, cw, pm, best = _gpu_decode(dec, q)
+    assert np.array_equal(cw, ref["cw"]) and np.array_equal(pm.astype(np.int64), ref["disc"])
+    assert np.array_equal(best, ref["best"])

@@ -207,3 +207,12 @@ def test_fer_matches_paper_figures(row):
     errs = int(np.sum(np.any(out["info"] != fr["u"], axis=1)))
     fer = errs / n_frames
     assert fer_paper / 2.2 <= fer <= fer_paper * 2.2, (fer, errs, n_frames, fer_paper)
+
+
+@pytest.mark.parametrize("m,r,P,L", [(5, 2, 4, 2), (7, 2, 8, 4), (9, 2, 20, 4), (9, 3, 16, 8), (6, 3, 2, 1)])
+def test_operation_count_model_matches_oracle_counter(m, r, P, L):
+    from paper_2108_12550_gb300 import opcount
+
+    fr = I.make_frames(m, r, 2, 2.0, seed=1)
+    o = O.decode(m, r, P, L, I.perm_table(m, r, P, L, seed=1), fr["llr"], want_ops=True)
+    assert np.all(o["ops"] == opcount.ops_per_frame(m, r, P, L))
