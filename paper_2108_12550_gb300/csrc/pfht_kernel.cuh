@@ -498,9 +498,8 @@ struct Decoder {
                 }
                 __syncwarp();
             }
-            if constexpr (PERM || ROOT) {
-                if (w.lane < L) ps.slot[S] = w.lane;
-            }
+            // this node's LLRs were just written with path l in slot l
+            if (w.lane < L) ps.slot[S] = w.lane;
             // f: left child RM(RR-1, S-1) (Algorithm 2, line 13)
             if constexpr (ROOT) {
 #pragma unroll 1

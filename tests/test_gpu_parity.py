@@ -114,7 +114,7 @@ def test_noiseless_frames_decode_exactly(m, r, P, L):
     nl = I.noiseless_frames(m, r, 64, seed=9)
     dec = pkg.Decoder(m, r, P, L, perm_seed=4)
     info, cw, pm, best = _gpu_decode(dec, nl["llr"].astype(np.float32))
-    assert np.array_equal(info, nl["u"]) and np.all(pm == 0)
+    assert np.array_equal(info, nl["u"]) and np.all(np.abs(pm) <= 1e-5 * np.abs(nl["llr"]).sum(axis=1))
 
 
 def test_library_seeded_tables_end_to_end():
