@@ -110,10 +110,14 @@ struct PState {
 };
 
 __device__ __forceinline__ float fminsum(float a, float b) {
-    // f(a, b) = min(|a|, |b|) sgn(a) sgn(b) (Section II-B), zero if either input is zero
-    float m = fminf(fabsf(a), fabsf(b));
-    float r = ((__float_as_uint(a) ^ __float_as_uint(b)) & 0x80000000u) ? -m : m;
-    return (a == 0.f || b == 0.f) ? 0.f : r;
+    // f(a, b) = min(|a|, |b|) sgn(a) sgn(b) (Section II-B). With a zero input the result is
+    // a signed zero, which every later step treats as 0 (hard decision 0, |.| = 0).
+    const float m = fminf(fabsf(a), fabsf(b));
+    return __uint_as_float(__float_as_uint(m) | ((__float_as_uint(a) ^ __float_as_uint(b)) & 0x80000000u));
+}
+// g(a, b, c) = b + (1 - 2c) a (Section II-B): the sign of a flipped when c = 1
+__device__ __forceinline__ float g_fn(float a, float b, unsigned c) {
+    return b + __uint_as_float(__float_as_uint(a) ^ (c << 31));
 }
 
 // i -> b ^ A v(i) of a record, for i with at most s significant bits
@@ -237,38 +241,73 @@ struct Decoder {
                 }
         // ... and over the lane bits
 #pragma unroll
-        for (int d = 1; d < G; d <<= 1)
+        for (int d = 1; d < G; d <<= 1) {
+            // lower index: u + w, upper index: u - w, as o + (+-1) v rounded once
+            const float sg = (g & d) ? -1.f : 1.f;
 #pragma unroll
             for (int e = 0; e < E; e++) {
                 const float o = __shfl_xor_sync(kFull, v[e], d);
-                v[e] = (g & d) ? (o - v[e]) : (v[e] + o);
+                v[e] = fmaf(sg, v[e], o);
             }
+        }
         const float pml = __shfl_sync(kFull, ps.pm, l);
+        // Each lane caches its two best candidates by (|c| descending, e ascending) and
+        // rescans (excluding taken entries) only when both were taken and another round
+        // remains. Rounds take the warp-wide minimum of (PM', l 2^S + k).
+        constexpr int DEPTH = E >= 2 ? 2 : 1;
         Mask taken = 0;
-        float babs = -1.f;
-        int be = 0;
-        bool bneg = false;
-        auto rescan = [&]() {
-            babs = -1.f;
-            be = 0;
-            bneg = false;
+        float c1 = 0.f, c2 = 0.f;
+        int e1 = 0, e2 = 0;
+        auto top2 = [&](Mask excl) {
+            bool h1 = false, h2 = false;
 #pragma unroll
             for (int e = 0; e < E; e++) {
-                const float av = fabsf(v[e]);
-                const bool ok = !((taken >> e) & 1) && av > babs;
-                babs = ok ? av : babs;
-                be = ok ? e : be;
-                bneg = ok ? (v[e] < 0.f) : bneg;
+                const float a = v[e];
+                const bool ok = !((excl >> e) & 1);
+                const bool g1 = ok && (!h1 || fabsf(a) > fabsf(c1));
+                const bool g2 = ok && !g1 && (!h2 || fabsf(a) > fabsf(c2));
+                c2 = g1 ? c1 : (g2 ? a : c2);
+                e2 = g1 ? e1 : (g2 ? e : e2);
+                h2 = h2 || g2 || (g1 && h1);
+                c1 = g1 ? a : c1;
+                e1 = g1 ? e : e1;
+                h1 = h1 || g1;
             }
+            return (h1 ? 1 : 0) + (h2 ? 1 : 0);
         };
-        rescan();
+        int avail = 0;
+        if constexpr (E == 1) {
+            c1 = v[0];
+            avail = 1;
+        } else {
+            // first pass without exclusions: the initial order is fixed by e = 0, 1
+            const bool g = fabsf(v[1]) > fabsf(v[0]);
+            c1 = g ? v[1] : v[0];
+            e1 = g ? 1 : 0;
+            c2 = g ? v[0] : v[1];
+            e2 = g ? 0 : 1;
+#pragma unroll
+            for (int e = 2; e < E; e++) {
+                const float a = v[e];
+                const bool g1 = fabsf(a) > fabsf(c1);
+                const bool g2 = fabsf(a) > fabsf(c2);
+                c2 = g1 ? c1 : (g2 ? a : c2);
+                e2 = g1 ? e1 : (g2 ? e : e2);
+                c1 = g1 ? a : c1;
+                e1 = g1 ? e : e1;
+            }
+            avail = 2;
+        }
+        int used = 0;
         int my_par = 0, my_k = 0, my_neg = 0;
         float my_pm = 0.f;
 #pragma unroll 1
         for (int q = 0; q < L; q++) {
-            float cpm = (act && babs >= 0.f) ? pml + 0.5f * (A - babs) : __int_as_float(0x7f800000);
-            int cidx = (l << S) | (g + G * be);
-            int cneg = bneg ? 1 : 0;
+            const float cc = used == 0 ? c1 : c2;
+            const int ce = used == 0 ? e1 : e2;
+            float cpm = (act && used < avail) ? pml + 0.5f * (A - fabsf(cc)) : __int_as_float(0x7f800000);
+            int cidx = (l << S) | (g + G * ce);
+            int cneg = cc < 0.f ? 1 : 0;
 #pragma unroll
             for (int d = 16; d >= 1; d >>= 1) {
                 const float opm = __shfl_xor_sync(kFull, cpm, d);
@@ -289,7 +328,15 @@ struct Decoder {
             const int owner = (cidx >> S) * G + (wk % G);
             if (w.lane == owner) {
                 taken |= Mask(1) << (wk / G);
-                rescan();
+                used++;
+            }
+            if constexpr (E > DEPTH) {
+                if (q + 1 < L && __any_sync(kFull, used == DEPTH)) {
+                    if (used == DEPTH) {
+                        avail = top2(taken);
+                        used = 0;
+                    }
+                }
             }
         }
         reselect<OFF, PEND>(w, ps, my_par, my_pm);
@@ -517,6 +564,14 @@ struct Decoder {
                         }
                     }
                 }
+            } else if constexpr (H >= 32) {
+#pragma unroll
+                for (int l = 0; l < L; l++)
+#pragma unroll
+                    for (int t = 0; t < H / 32; t++) {
+                        const int i = w.lane + 32 * t;
+                        child[l * STC + i] = fminsum(nodebuf[l * STN + i], nodebuf[l * STN + i + H]);
+                    }
             } else {
 #pragma unroll
                 for (int it = 0; it < (L * H + 31) / 32; it++) {
@@ -543,10 +598,22 @@ struct Decoder {
                         const int i = w.lane + 32 * t;
                         if (i < H) {
                             const int j = base ^ ga_hi(r, S - 1, t);
-                            const int xb = (bl[(OFF + i) >> 5] >> ((OFF + i) & 31)) & 1;
-                            const float u = w.y[j], v = w.y[j ^ a];
-                            child[l * STC + i] = xb ? v - u : v + u;
+                            const unsigned xb = (bl[(OFF + i) >> 5] >> ((OFF + i) & 31)) & 1u;
+                            child[l * STC + i] = g_fn(w.y[j], w.y[j ^ a], xb);
                         }
+                    }
+                }
+            } else if constexpr (H >= 32) {
+                static_assert(OFF % 32 == 0, "spans of 64 or more bits are word aligned");
+#pragma unroll
+                for (int l = 0; l < L; l++) {
+                    const int sl = __shfl_sync(kFull, ps.slot[S], l);
+                    const uint32_t* bl = bitbuf(w, w.bsel, l) + OFF / 32;
+                    const float* src = nodebuf + sl * STN;
+#pragma unroll
+                    for (int t = 0; t < H / 32; t++) {
+                        const int i = w.lane + 32 * t;
+                        child[l * STC + i] = g_fn(src[i], src[i + H], (bl[t] >> w.lane) & 1u);
                     }
                 }
             } else {
@@ -558,9 +625,8 @@ struct Decoder {
                     if (idx < L * H) {
                         const int i = idx % H;
                         const uint32_t* bl = bitbuf(w, w.bsel, l);
-                        const int xb = (bl[(OFF + i) >> 5] >> ((OFF + i) & 31)) & 1;
-                        const float u = nodebuf[sl * STN + i], v = nodebuf[sl * STN + i + H];
-                        child[l * STC + i] = xb ? v - u : v + u;
+                        const unsigned xb = (bl[(OFF + i) >> 5] >> ((OFF + i) & 31)) & 1u;
+                        child[l * STC + i] = g_fn(nodebuf[sl * STN + i], nodebuf[sl * STN + i + H], xb);
                     }
                 }
             }
@@ -674,7 +740,7 @@ struct Decoder {
 };
 
 template <int M, int R, int L>
-__global__ void __launch_bounds__(256) pfht_kernel(LaunchArgs args) {
+__global__ void __launch_bounds__(128, 4) pfht_kernel(LaunchArgs args) {
     using C = Cfg<M, R, L>;
     using D = Decoder<M, R, L>;
     constexpr int N = C::N;

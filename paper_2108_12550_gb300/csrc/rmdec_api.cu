@@ -224,7 +224,7 @@ rmdec_status ensure_device(rmdec_ctx* h) {
     if ((e = cudaMemcpy(h->d_info, info16.data(), info16.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess) return h->cuda_fail(e, "upload info");
     // warps per CTA: decoders of one frame split across warps
     int W = h->algo == 0 ? std::min(h->P, 4) : 4;
-    if (const char* s = getenv("RMDEC_WARPS")) W = std::max(1, std::min(8, atoi(s)));
+    if (const char* s = getenv("RMDEC_WARPS")) W = std::max(1, std::min(4, atoi(s)));
     h->warps = W;
     h->smem = (size_t)h->kern.fixed_bytes(h->P, h->k, W) + 16 + (size_t)W * h->kern.warp_bytes;
     int max_optin = 0;
