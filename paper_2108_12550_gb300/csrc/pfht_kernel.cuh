@@ -147,6 +147,14 @@ __device__ __forceinline__ int ga_hi(const uint16_t* r, int s, int t32) {
 __device__ __forceinline__ int insert_zero(int x, int h) {  // insert a 0 bit at position h
     return ((x >> h) << (h + 1)) | (x & ((1 << h) - 1));
 }
+// Order-preserving map of IEEE single to unsigned (for integer warp reductions) and back.
+__device__ __forceinline__ unsigned ordered_bits(float f) {
+    const unsigned b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float ordered_float(unsigned u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
@@ -224,9 +232,17 @@ struct Decoder {
         float v[E];
 #pragma unroll
         for (int e = 0; e < E; e++) v[e] = act ? buf[l * ST + g + G * e] : 0.f;
-        float A = 0.f;
+        float A;
+        {
+            float t[E];
 #pragma unroll
-        for (int e = 0; e < E; e++) A += fabsf(v[e]);
+            for (int e = 0; e < E; e++) t[e] = fabsf(v[e]);
+#pragma unroll
+            for (int h = E / 2; h >= 1; h >>= 1)
+#pragma unroll
+                for (int e = 0; e < h; e++) t[e] += t[e + h];
+            A = t[0];
+        }
 #pragma unroll
         for (int d = 1; d < G; d <<= 1) A += __shfl_xor_sync(kFull, A, d);
         // butterflies (u, w) -> (u + w, u - w) over the register bits of the index ...
@@ -258,44 +274,55 @@ struct Decoder {
         Mask taken = 0;
         float c1 = 0.f, c2 = 0.f;
         int e1 = 0, e2 = 0;
-        auto top2 = [&](Mask excl) {
-            bool h1 = false, h2 = false;
-#pragma unroll
-            for (int e = 0; e < E; e++) {
-                const float a = v[e];
-                const bool ok = !((excl >> e) & 1);
-                const bool g1 = ok && (!h1 || fabsf(a) > fabsf(c1));
-                const bool g2 = ok && !g1 && (!h2 || fabsf(a) > fabsf(c2));
-                c2 = g1 ? c1 : (g2 ? a : c2);
-                e2 = g1 ? e1 : (g2 ? e : e2);
-                h2 = h2 || g2 || (g1 && h1);
-                c1 = g1 ? a : c1;
-                e1 = g1 ? e : e1;
-                h1 = h1 || g1;
-            }
-            return (h1 ? 1 : 0) + (h2 ? 1 : 0);
-        };
         int avail = 0;
+        // (x, ex) ranks before (y, ey): larger |value|, then smaller index
+        auto better = [](float x, int ex, float y, int ey) {
+            return fabsf(x) > fabsf(y) || (fabsf(x) == fabsf(y) && ex < ey);
+        };
         if constexpr (E == 1) {
             c1 = v[0];
             avail = 1;
+        } else if constexpr (E == 2) {
+            const bool gg = fabsf(v[1]) > fabsf(v[0]);
+            c1 = gg ? v[1] : v[0];
+            e1 = gg ? 1 : 0;
+            c2 = gg ? v[0] : v[1];
+            e2 = gg ? 0 : 1;
+            avail = 2;
         } else {
-            // first pass without exclusions: the initial order is fixed by e = 0, 1
-            const bool g = fabsf(v[1]) > fabsf(v[0]);
-            c1 = g ? v[1] : v[0];
-            e1 = g ? 1 : 0;
-            c2 = g ? v[0] : v[1];
-            e2 = g ? 0 : 1;
+            // two independent scans (even and odd e) shorten the dependency chain; each keeps
+            // its two best in (|c| descending, e ascending) order, then the lists merge
+            float a1[2], a2[2];
+            int i1[2], i2[2];
 #pragma unroll
-            for (int e = 2; e < E; e++) {
-                const float a = v[e];
-                const bool g1 = fabsf(a) > fabsf(c1);
-                const bool g2 = fabsf(a) > fabsf(c2);
-                c2 = g1 ? c1 : (g2 ? a : c2);
-                e2 = g1 ? e1 : (g2 ? e : e2);
-                c1 = g1 ? a : c1;
-                e1 = g1 ? e : e1;
+            for (int h = 0; h < 2; h++) {
+                const bool gg = fabsf(v[h + 2]) > fabsf(v[h]);
+                a1[h] = gg ? v[h + 2] : v[h];
+                i1[h] = gg ? h + 2 : h;
+                a2[h] = gg ? v[h] : v[h + 2];
+                i2[h] = gg ? h : h + 2;
             }
+#pragma unroll
+            for (int e = 4; e < E; e++) {
+                const int h = e & 1;
+                const float a = v[e];
+                const bool g1 = fabsf(a) > fabsf(a1[h]);
+                const bool g2 = fabsf(a) > fabsf(a2[h]);
+                a2[h] = g1 ? a1[h] : (g2 ? a : a2[h]);
+                i2[h] = g1 ? i1[h] : (g2 ? e : i2[h]);
+                a1[h] = g1 ? a : a1[h];
+                i1[h] = g1 ? e : i1[h];
+            }
+            const bool f0 = better(a1[0], i1[0], a1[1], i1[1]);
+            c1 = f0 ? a1[0] : a1[1];
+            e1 = f0 ? i1[0] : i1[1];
+            const float sa = f0 ? a2[0] : a1[0];
+            const int sai = f0 ? i2[0] : i1[0];
+            const float sb = f0 ? a1[1] : a2[1];
+            const int sbi = f0 ? i1[1] : i2[1];
+            const bool f1 = better(sa, sai, sb, sbi);
+            c2 = f1 ? sa : sb;
+            e2 = f1 ? sai : sbi;
             avail = 2;
         }
         int used = 0;
@@ -305,24 +332,19 @@ struct Decoder {
         for (int q = 0; q < L; q++) {
             const float cc = used == 0 ? c1 : c2;
             const int ce = used == 0 ? e1 : e2;
-            float cpm = (act && used < avail) ? pml + 0.5f * (A - fabsf(cc)) : __int_as_float(0x7f800000);
-            int cidx = (l << S) | (g + G * ce);
-            int cneg = cc < 0.f ? 1 : 0;
-#pragma unroll
-            for (int d = 16; d >= 1; d >>= 1) {
-                const float opm = __shfl_xor_sync(kFull, cpm, d);
-                const int oidx = __shfl_xor_sync(kFull, cidx, d);
-                const int oneg = __shfl_xor_sync(kFull, cneg, d);
-                const bool take = (opm < cpm) || (opm == cpm && oidx < cidx);
-                cpm = take ? opm : cpm;
-                cidx = take ? oidx : cidx;
-                cneg = take ? oneg : cneg;
-            }
+            const float cpm = (act && used < avail) ? pml + 0.5f * (A - fabsf(cc)) : __int_as_float(0x7f800000);
+            const unsigned cid = ((unsigned)((l << S) | (g + G * ce)) << 1) | (cc < 0.f ? 1u : 0u);
+            // warp minimum of (PM', l 2^S + k): two single-instruction reductions on an
+            // order-preserving integer image of PM', then on the index among the tied lanes
+            const unsigned key = ordered_bits(cpm);
+            const unsigned kmin = __reduce_min_sync(kFull, key);
+            const unsigned imin = __reduce_min_sync(kFull, key == kmin ? cid : 0xffffffffu);
+            const int cidx = (int)(imin >> 1);
             if (w.lane == q) {
-                my_pm = cpm;
+                my_pm = ordered_float(kmin);
                 my_par = cidx >> S;
                 my_k = cidx & ((1 << S) - 1);
-                my_neg = cneg;
+                my_neg = (int)(imin & 1u);
             }
             const int wk = cidx & ((1 << S) - 1);
             const int owner = (cidx >> S) * G + (wk % G);
@@ -332,10 +354,39 @@ struct Decoder {
             }
             if constexpr (E > DEPTH) {
                 if (q + 1 < L && __any_sync(kFull, used == DEPTH)) {
-                    if (used == DEPTH) {
-                        avail = top2(taken);
+                    // rare: a lane gave away both cached candidates. The node's input buffer
+                    // is free now; park the spectrum there and rescan it with a rolled loop.
+                    float* vb = const_cast<float*>(buf) + l * ST + g;
+                    if (act) {
+#pragma unroll
+                        for (int e = 0; e < E; e++) vb[G * e] = v[e];
+                    }
+                    __syncwarp();
+                    if (act && used == DEPTH) {
+                        bool h1 = false, h2 = false;
+#pragma unroll 1
+                        for (int e = 0; e < E; e++) {
+                            if ((taken >> e) & 1) continue;
+                            const float a = vb[G * e];
+                            const bool g1 = !h1 || fabsf(a) > fabsf(c1);
+                            const bool g2 = !g1 && (!h2 || fabsf(a) > fabsf(c2));
+                            if (g1) {
+                                c2 = c1;
+                                e2 = e1;
+                                h2 = h1;
+                                c1 = a;
+                                e1 = e;
+                                h1 = true;
+                            } else if (g2) {
+                                c2 = a;
+                                e2 = e;
+                                h2 = true;
+                            }
+                        }
+                        avail = (h1 ? 1 : 0) + (h2 ? 1 : 0);
                         used = 0;
                     }
+                    __syncwarp();
                 }
             }
         }
@@ -404,25 +455,30 @@ struct Decoder {
         }
         __syncwarp();
         const int me = w.lane < L ? w.lane : 0;
-        unsigned hd = 0;
-        const float* am = buf + me * ST;
+        float pm;
+        int p;
+        {
+            const float* am = buf + me * ST;
+            unsigned hd0 = 0;
 #pragma unroll
-        for (int i = 0; i < NS; i++) hd |= (am[i] < 0.f ? 1u : 0u) << i;
-        int o0 = w.spc[me * 32];
-        float lrb = fabsf(am[o0]);
-        int p = __popc(hd) & 1;
-        float pm = ps.pm + (p ? lrb : 0.f);  // Eq. (3)
+            for (int i = 0; i < NS; i++) hd0 |= (am[i] < 0.f ? 1u : 0u) << i;
+            p = __popc(hd0) & 1;
+            pm = ps.pm + (p ? fabsf(am[w.spc[me * 32]]) : 0.f);  // Eq. (3)
+        }
         unsigned flip = 0;
         int orig = me;
 #pragma unroll 1
         for (int t = 1; t <= TAU; t++) {
+            // the split position and the LRB belong to the path's SPC-entry ancestor `orig`
+            const float* ao = buf + orig * ST;
             const int itp = w.spc[orig * 32 + t];
-            const float at = fabsf(buf[orig * ST + itp]);
-            const float pflip = pm + at + (p ? -lrb : lrb);  // Eq. (4)
+            const float lrb = fabsf(ao[w.spc[orig * 32]]);
+            const float pflip = pm + fabsf(ao[itp]) + (p ? -lrb : lrb);  // Eq. (4)
             const int src = w.lane < 2 * L ? (w.lane >> 1) : 0;
             const float kpm = __shfl_sync(kFull, pm, src);
             const float fpm = __shfl_sync(kFull, pflip, src);
             const float cpm = (w.lane & 1) ? fpm : kpm;
+            // rank of candidate `lane` among the 2L by (PM, 2l + flip)
             int rank = 0;
 #pragma unroll
             for (int c2 = 0; c2 < 2 * L; c2++) {
@@ -437,25 +493,28 @@ struct Decoder {
             }
             const int sp = mysrc >> 1;
             const bool fl = mysrc & 1;
+            // state of the source path: metric, ancestor, flips, parity, split position
             const float n_kpm = __shfl_sync(kFull, pm, sp);
             const float n_fpm = __shfl_sync(kFull, pflip, sp);
-            const int n_orig = __shfl_sync(kFull, orig, sp);
+            const float n_pm = fl ? n_fpm : n_kpm;
+            const unsigned packed = __shfl_sync(kFull, (unsigned)orig | ((unsigned)p << 8) | ((unsigned)itp << 16), sp);
             const unsigned n_flip = __shfl_sync(kFull, flip, sp);
-            const int n_p = __shfl_sync(kFull, p, sp);
-            const float n_lrb = __shfl_sync(kFull, lrb, sp);
-            const int n_o0 = __shfl_sync(kFull, o0, sp);
-            const unsigned n_hd = __shfl_sync(kFull, hd, sp);
-            const int n_it = __shfl_sync(kFull, itp, sp);
-            pm = fl ? n_fpm : n_kpm;
-            orig = n_orig;
+            pm = n_pm;
+            orig = (int)(packed & 0xffu);
+            const int n_it = (int)(packed >> 16);
             flip = fl ? (n_flip ^ (1u << n_it)) : n_flip;  // Eq. (5)
-            p = fl ? (n_p ^ 1) : n_p;
-            lrb = n_lrb;
-            o0 = n_o0;
-            hd = n_hd;
+            p = fl ? (int)(((packed >> 8) & 1u) ^ 1u) : (int)((packed >> 8) & 1u);
         }
-        unsigned x = (hd ^ flip) & ~(1u << o0);
-        x |= (unsigned)(__popc(x) & 1) << o0;  // Eq. (6)
+        unsigned x;
+        {
+            const float* ao = buf + orig * ST;
+            unsigned hd = 0;
+#pragma unroll
+            for (int i = 0; i < NS; i++) hd |= (ao[i] < 0.f ? 1u : 0u) << i;
+            const int o0 = w.spc[orig * 32];
+            x = (hd ^ flip) & ~(1u << o0);
+            x |= (unsigned)(__popc(x) & 1) << o0;  // Eq. (6)
+        }
         reselect<OFF, PEND>(w, ps, orig, pm);
         put_small_bits<OFF, NS>(w, x);
     }
@@ -471,13 +530,13 @@ struct Decoder {
     __device__ static int select_perms(Warp& w, const uint16_t* recs, Src src) {
         constexpr int C2 = 2 * L;
         constexpr int HALF = 1 << (S - 1);
-        float lm[C2];
-#pragma unroll
+        float mylm = 0.f;  // lane c keeps LM_c
+#pragma unroll 1
         for (int c = 0; c < C2; c++) {
             const uint16_t* r = recs + c * kRec;
             const int a = r[S - 1];
             const int h = 31 - __clz(a);
-            const int lorg = c % L;
+            const int lorg = c & (L - 1);
             float acc = 0.f;
 #pragma unroll
             for (int t = 0; t < (HALF + 31) / 32; t++) {
@@ -487,15 +546,21 @@ struct Decoder {
                     acc += fminf(fabsf(src(lorg, j)), fabsf(src(lorg, j ^ a)));
                 }
             }
-            lm[c] = warp_sum(acc);
+            acc = warp_sum(acc);
+            if (w.lane == c) mylm = acc;
+        }
+        // rank of candidate `lane` by (LM descending, c ascending); lane q < L takes rank q
+        int rank = 0;
+#pragma unroll
+        for (int c2 = 0; c2 < C2; c2++) {
+            const float o = __shfl_sync(kFull, mylm, c2);
+            rank += (o > mylm) || (o == mylm && c2 < w.lane);
         }
         int mine = 0;
 #pragma unroll
-        for (int c = 0; c < C2; c++) {
-            int rank = 0;
-#pragma unroll
-            for (int c2 = 0; c2 < C2; c2++) rank += (lm[c2] > lm[c]) || (lm[c2] == lm[c] && c2 < c);
-            if (rank == w.lane) mine = c;
+        for (int q = 0; q < L; q++) {
+            const unsigned b = __ballot_sync(kFull, w.lane < C2 && rank == q);
+            if (w.lane == q) mine = __ffs(b) - 1;
         }
         return mine;
     }
@@ -565,7 +630,7 @@ struct Decoder {
                     }
                 }
             } else if constexpr (H >= 32) {
-#pragma unroll
+#pragma unroll 1
                 for (int l = 0; l < L; l++)
 #pragma unroll
                     for (int t = 0; t < H / 32; t++) {
@@ -605,7 +670,7 @@ struct Decoder {
                 }
             } else if constexpr (H >= 32) {
                 static_assert(OFF % 32 == 0, "spans of 64 or more bits are word aligned");
-#pragma unroll
+#pragma unroll 1
                 for (int l = 0; l < L; l++) {
                     const int sl = __shfl_sync(kFull, ps.slot[S], l);
                     const uint32_t* bl = bitbuf(w, w.bsel, l) + OFF / 32;
@@ -697,9 +762,9 @@ struct Decoder {
         }
     }
 
-    // Runs one decoder (Algorithm 2 from the root) and returns the best path's metric; the
-    // best path's codeword in the channel domain is left in w.xtmp.
-    __device__ static float run(Warp& w) {
+    // Runs one decoder (Algorithm 2 from the root); returns the best path's metric and its
+    // root permutation. The path's bits stay in its bit buffer (see emit()).
+    __device__ static float run(Warp& w, int& c0) {
         PState<M> ps;
         ps.pm = 0.f;
         ps.rootc = 0;
@@ -711,8 +776,14 @@ struct Decoder {
         w.bsel = 0;
         node<R, M, 0, true, true, 0u>(w, ps);
         // the list is sorted by metric: path 0 is the decoder's best (Algorithm 5, line 5)
-        const float pm0 = __shfl_sync(kFull, ps.pm, 0);
-        const int c0 = __shfl_sync(kFull, ps.rootc, 0);
+        c0 = __shfl_sync(kFull, ps.rootc, 0);
+        return __shfl_sync(kFull, ps.pm, 0);
+    }
+
+    // Root combine and un-permutation of path 0 into `dst` (the codeword in the channel
+    // domain): x_root = (x_gamma ^ x_lambda, x_gamma), then x[sigma(i)] = x'[i] with
+    // sigma = pi^init o pi* the path's composed root permutation (Algorithm 2, lines 17-21).
+    __device__ static void emit(Warp& w, int c0, uint32_t* dst) {
         uint32_t* b = bitbuf(w, w.bsel, 0);
         constexpr int H = N / 2;
         if constexpr (H >= 32) {
@@ -720,22 +791,19 @@ struct Decoder {
         } else if (w.lane == 0) {
             b[0] ^= (b[0] >> H) & ((1u << H) - 1u);
         }
+        for (int wd = w.lane; wd < NW; wd += 32) dst[wd] = 0;
         __syncwarp();
-        // undo the root permutation sigma = pi^init o pi*: x[sigma(i)] = x'[i]
         const uint16_t* r = w.rec + c0 * kRec;
-        for (int wd = w.lane; wd < NW; wd += 32) w.xtmp[wd] = 0;
-        __syncwarp();
         const int base = ga_lane_base(r, M, w.lane);
 #pragma unroll
         for (int t = 0; t < (N + 31) / 32; t++) {
             const int i = w.lane + 32 * t;
             if (i < N) {
                 const int dstp = base ^ ga_hi(r, M, t);
-                if ((b[i >> 5] >> (i & 31)) & 1u) atomicOr(&w.xtmp[dstp >> 5], 1u << (dstp & 31));
+                if ((b[i >> 5] >> (i & 31)) & 1u) atomicOr(&dst[dstp >> 5], 1u << (dstp & 31));
             }
         }
         __syncwarp();
-        return pm0;
     }
 };
 
@@ -793,11 +861,12 @@ __global__ void __launch_bounds__(128, 4) pfht_kernel(LaunchArgs args) {
         int bestp = -1;
         for (int p = warp; p < P; p += W) {
             w.rec = s_rec + p * C::NREC * kRec;
-            const float pm = D::run(w);
+            int c0;
+            const float pm = D::run(w, c0);
             if (bestp < 0 || pm < best) {  // strict: earlier decoders win ties (Algorithm 5)
                 best = pm;
                 bestp = p;
-                for (int wd = lane; wd < NW; wd += 32) w.best[wd] = w.xtmp[wd];
+                D::emit(w, c0, w.best);
             }
             __syncwarp();
         }
