@@ -24,6 +24,7 @@ sys.path.insert(0, ROOT)
 
 from paper_2108_12550_gb300 import inputs as I  # noqa: E402
 from paper_2108_12550_gb300 import opcount  # noqa: E402
+from paper_2108_12550_gb300 import replicas  # noqa: E402
 
 WORKLOADS = {
     # name: (m, r, P, L, EbN0 dB, frames per step)
@@ -150,19 +151,107 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args):
+    """Serving mix: Poisson arrivals of requests over 16 decoder configurations; the
+    continuous-batching server against a plain per-request launch on the same trace."""
+    import torch
+
+    import paper_2108_12550_gb300 as pkg
+
+    codes = [(m, r) for (m, r) in [(7, 2), (8, 2), (9, 2), (9, 3)]]
+    cfgs = [(m, r, P, 4, dt) for (m, r) in codes for P in (8, 20) for dt in ("i8", "f32")]
+    decs = [pkg.Decoder(m, r, P, L, perm_seed=1 + i, dtype=dt) for i, (m, r, P, L, dt) in enumerate(cfgs)]
+    rng = np.random.default_rng(7)
+    pool_frames = 4096
+    pools = {}  # (config, Eb/N0 bucket) -> pinned LLRs
+    for ci, (m, r, P, L, dt) in enumerate(cfgs):
+        for bi, eb in enumerate((2.0, 3.0, 4.0, 5.0)):
+            llr, _ = _frames(m, r, pool_frames, eb, seed=1000 + ci * 10 + bi, chunk=pool_frames)
+            x = I.quantize_i8(llr) if dt == "i8" else llr
+            pools[(ci, bi)] = torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    n_req = args.requests
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, n_req))
+    trace = []
+    for q in range(n_req):
+        ci = int(rng.integers(len(cfgs)))
+        nf = int(np.exp(rng.uniform(0.0, np.log(4096))))
+        bi = min(3, int(rng.uniform(2.0, 5.0) - 2.0))
+        off = int(rng.integers(0, pool_frames - nf + 1))
+        x = pools[(ci, bi)][off:off + nf]
+        out = torch.zeros((nf, decs[ci].kw), dtype=torch.int32).pin_memory()
+        trace.append((ci, x, out, float(arrivals[q])))
+    total_frames = sum(t[1].shape[0] for t in trace)
+    for ci, d in enumerate(decs):  # build device tables and grow staging to the largest request
+        d.decode_host(pools[(ci, 0)], torch.zeros((pool_frames, d.kw), dtype=torch.int32))
+    torch.cuda.synchronize()
+
+    # continuous-batching server
+    srv = pkg.Server(n_streams=args.streams, arena_bytes=2 << 30, max_batch_frames=1 << 15,
+                     min_batch_frames=1024, max_wait_us=500)
+    ids = [srv.add_decoder(d) for d in decs]
+    t0 = time.perf_counter()
+    rids = []
+    for ci, x, out, at in trace:
+        while time.perf_counter() - t0 < at:
+            pass
+        rids.append(srv.submit(ids[ci], x, out))
+    lat = []
+    for rid in rids:
+        st, l_us = srv.poll(rid, timeout_us=120_000_000)
+        if st != pkg.OK:
+            raise RuntimeError(f"serving request failed: {st}")
+        lat.append(l_us)
+    t_srv = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
+    served = [t[2].clone() for t in trace]
+
+    # plain per-request launch: one synchronous host-to-host decode per request, in order
+    s = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    plat = []
+    for ci, x, out, at in trace:
+        while time.perf_counter() - t0 < at:
+            pass
+        decs[ci].decode_host(x, out, s)
+        plat.append((time.perf_counter() - t0 - at) * 1e6)
+    t_plain = time.perf_counter() - t0
+    same = all(torch.equal(a, t[2]) for a, t in zip(served, trace))
+    line = {
+        "metric": "frames/s serving mix (Poisson arrivals, mixed RM codes, P in {8,20}, L=4, INT8/FP32)",
+        "value": total_frames / t_srv, "unit": "frames/s", "n_gpus": 1, "higher_is_better": True,
+        "dtype": "mixed i8/f32", "data": "synthetic",
+        "config": {"workload": "serving_mix", "requests": n_req, "rate_per_s": args.rate, "frames": total_frames,
+                   "streams": args.streams, "codes": ["RM(2,7)", "RM(2,8)", "RM(2,9)", "RM(3,9)"]},
+        "latency_us": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "max": float(np.max(lat))},
+        "server": {k: stats[k] for k in ("batches", "completed", "frames_completed")},
+        "plain_per_request": {"value": total_frames / t_plain, "unit": "frames/s",
+                              "latency_us": {"p50": float(np.percentile(plat, 50)),
+                                             "p99": float(np.percentile(plat, 99))}},
+        "results_identical_alone_and_in_mix": bool(same),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="rm29_p20_l4", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="rm29_p20_l4", choices=sorted(WORKLOADS) + ["serving_mix"])
+    ap.add_argument("--requests", type=int, default=2000, help="serving mix: requests in the trace")
+    ap.add_argument("--rate", type=float, default=4000.0, help="serving mix: Poisson arrivals per second")
+    ap.add_argument("--streams", type=int, default=4, help="serving mix: server CUDA streams")
     ap.add_argument("--frames", type=int, default=0, help="frames per step (default per workload)")
     ap.add_argument("--dtype", default="f32", choices=["f32", "i8", "f16", "i16"])
     ap.add_argument("--cpu-frames", type=int, default=1500, help="CPU-baseline sample size")
     ap.add_argument("--ref-frames", type=int, default=1000, help="frames per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.workload == "serving_mix":
+        return run_serving(args)
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl)
@@ -210,15 +299,13 @@ def main():
         ev1.record(stream)
         barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
-    t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = replicas.allreduce_max(ms, device="cuda")  # the job is as slow as its slowest rank
     value = nf * world / (ms_max * 1e-3)
 
-    # correctness side-channel: frame error rate of the timed batch vs the transmitted messages
+    # correctness side-channel: frame error rate of the timed batches vs the transmitted messages
     got = pkg.unpack_bits(out.cpu().numpy(), k)
-    fer = float(np.mean(np.any(got != u_np, axis=1)))
+    errs, frames = replicas.allreduce_sum([int(np.sum(np.any(got != u_np, axis=1))), nf], device="cuda")
+    fer = errs / frames
 
     # end to end through the host entry point: pinned host LLRs in, information bits out
     host_in = torch.from_numpy(llr_np).pin_memory()
@@ -231,10 +318,7 @@ def main():
         dec.decode_host(host_in, host_out, stream)
     barrier()
     e_ms = (time.perf_counter() - e0) / e_steps * 1e3
-    te = torch.tensor([e_ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e_value = nf * world / (float(te.item()) * 1e-3)
+    e_value = nf * world / (replicas.allreduce_max(e_ms, device="cuda") * 1e-3)
 
     pk, src = _peaks()
     sm_mhz = float(pk.get("sm_max_mhz", 2070.0))

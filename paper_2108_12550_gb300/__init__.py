@@ -197,3 +197,94 @@ def pack_bits(bits):
     pad = np.zeros((F, W * 32), dtype=np.uint32)
     pad[:, :n] = b
     return (pad.reshape(F, W, 32) << np.arange(32, dtype=np.uint32)).sum(axis=2).astype(np.uint32)
+
+
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("n_streams", ctypes.c_int), ("arena_bytes", ctypes.c_int64),
+                ("max_batch_frames", ctypes.c_int64), ("min_batch_frames", ctypes.c_int64),
+                ("max_wait_us", ctypes.c_int64)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("frames_completed", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("in_flight", ctypes.c_int64),
+                ("latency_p50_us", ctypes.c_double), ("latency_p99_us", ctypes.c_double),
+                ("latency_max_us", ctypes.c_double), ("busy_seconds", ctypes.c_double)]
+
+
+def _load_server_api(lib):
+    if getattr(lib, "_server_sigs", False):
+        return lib
+    V, I, I64, U64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    sig = {
+        "rmdec_server_create": ([ctypes.POINTER(V), ctypes.POINTER(_ServerConfig)], I),
+        "rmdec_server_add_decoder": ([V, V, ctypes.POINTER(I)], I),
+        "rmdec_server_submit": ([V, I, V, I64, V, ctypes.POINTER(U64)], I),
+        "rmdec_server_poll": ([V, U64, I64, ctypes.POINTER(D)], I),
+        "rmdec_server_stats_get": ([V, ctypes.POINTER(_ServerStats)], I),
+        "rmdec_server_destroy": ([V], None),
+        "rmdec_server_last_error": ([V], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    lib._server_sigs = True
+    return lib
+
+
+class Server:
+    """Continuous-batching request server (include/rmdec_serve.h) over Decoder handles."""
+
+    def __init__(self, n_streams=4, arena_bytes=1 << 30, max_batch_frames=1 << 16, min_batch_frames=0,
+                 max_wait_us=0):
+        self._lib = _load_server_api(load_library())
+        cfg = _ServerConfig(n_streams, arena_bytes, max_batch_frames, min_batch_frames, max_wait_us)
+        h = ctypes.c_void_p()
+        st = self._lib.rmdec_server_create(ctypes.byref(h), ctypes.byref(cfg))
+        if st != OK:
+            raise RmdecError(st, self._lib.rmdec_server_last_error(None).decode())
+        self._h = h
+        self._decoders = []
+
+    def _check(self, st):
+        if st != OK:
+            raise RmdecError(st, self._lib.rmdec_server_last_error(self._h).decode())
+
+    def add_decoder(self, dec):
+        cid = ctypes.c_int()
+        self._check(self._lib.rmdec_server_add_decoder(self._h, dec._h, ctypes.byref(cid)))
+        self._decoders.append(dec)  # keep the handle alive for the server's lifetime
+        return cid.value
+
+    def submit(self, code_id, llr_host, out_host):
+        """llr_host / out_host: CPU tensors (pinned for speed) that outlive the request."""
+        rid = ctypes.c_uint64()
+        self._check(self._lib.rmdec_server_submit(self._h, code_id, llr_host.data_ptr(), llr_host.shape[0],
+                                                  out_host.data_ptr(), ctypes.byref(rid)))
+        return rid.value
+
+    def poll(self, request, timeout_us=0):
+        """Returns (status, latency_us); status OK, EBUSY or ETIMEDOUT (others raise)."""
+        lat = ctypes.c_double(-1.0)
+        st = self._lib.rmdec_server_poll(self._h, request, int(timeout_us), ctypes.byref(lat))
+        if st in (OK, EBUSY, ETIMEDOUT):
+            return st, lat.value
+        self._check(st)
+
+    def stats(self):
+        s = _ServerStats()
+        self._check(self._lib.rmdec_server_stats_get(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in _ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.rmdec_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

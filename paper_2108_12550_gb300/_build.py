@@ -16,7 +16,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
                      "--expt-relaxed-constexpr"]
 
-UNITS = ["rmdec_api.cu", "autssc.cu"] + [f"inst_m{m}.cu" for m in range(4, 10)]
+UNITS = ["rmdec_api.cu", "autssc.cu", "serve.cu"] + [f"inst_m{m}.cu" for m in range(4, 10)]
 HEADERS = ["pfht_kernel.cuh", "rmdec_internal.h"]
 
 
@@ -37,7 +37,8 @@ def _stale(target: str, deps: list[str]) -> bool:
 def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
-    hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "rmdec.h")]
+    hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", h)
+                                                        for h in ("rmdec.h", "rmdec_serve.h")]
     objs, todo = [], []
     for u in UNITS:
         src = os.path.join(CSRC, u)

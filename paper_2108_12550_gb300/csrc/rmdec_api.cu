@@ -317,6 +317,10 @@ rmdec_status make_handle(rmdec_t* out, int algo, int m, int r, int P, int L, uin
 
 }  // namespace
 
+namespace rmdec_host {
+size_t llr_elem_bytes_of(rmdec_ctx* h) { return llr_elem_bytes(h->dtype); }
+}  // namespace rmdec_host
+
 extern "C" {
 
 rmdec_status rmdec_create(rmdec_t* out, int m, int r, int P, int L, uint64_t perm_seed) {

@@ -1,11 +1,17 @@
 // Internal interfaces between the C-ABI layer and the kernel instantiation units.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 
 #include <cuda_runtime.h>
 
+struct rmdec_ctx;
+
 namespace rmdec_host {
+
+// Bytes per LLR element of a handle's current input type.
+size_t llr_elem_bytes_of(rmdec_ctx* h);
 
 // One compiled decoder configuration (a kernel template instance).
 struct KernelEntry {
