@@ -122,6 +122,29 @@ rmdec_status rmdec_submit(rmdec_t h, const void *llr_dev, int64_t n_frames, uint
  * RMDEC_ETIMEDOUT if the wait expired, RMDEC_EINVAL for an unknown ticket. */
 rmdec_status rmdec_poll(rmdec_t h, uint64_t ticket, int64_t timeout_us);
 
+/* Launch shape: warps per CTA (1..4; the decoders of a frame are split across a CTA's warps)
+ * and a cap on resident CTAs per SM (0 = the occupancy limit). Takes effect on the next
+ * decode. Not part of the paper's method: it only changes scheduling, never results. */
+rmdec_status rmdec_set_tuning(rmdec_t h, int warps_per_cta, int ctas_per_sm);
+rmdec_status rmdec_get_tuning(rmdec_t h, int *warps_per_cta, int *ctas_per_sm);
+
+/* Times every candidate launch shape on n_frames synthetic frames (allocated and freed inside
+ * this call; synchronous on `stream`) and keeps the fastest. With a non-NULL cache_path, a
+ * choice stored there for the same device, code, P, L and dtype is reused without timing, and a
+ * new choice is appended (one text line per entry). Call before any stream capture. */
+rmdec_status rmdec_autotune(rmdec_t h, int64_t n_frames, const char *cache_path, void *stream);
+
+/* A captured host-to-host decode pipeline for fixed buffers: copy n_frames LLRs from
+ * llr_host, decode, copy the information bits to bits_out_host (layouts as in
+ * rmdec_decode_host), recorded once as a CUDA graph and replayed with one launch. The graph
+ * owns its device buffers; the host buffers must outlive it (pinned memory recommended). */
+typedef struct rmdec_graph *rmdec_graph_t;
+rmdec_status rmdec_graph_create(rmdec_t h, const void *llr_host, int64_t n_frames, uint32_t *bits_out_host,
+                                rmdec_graph_t *out);
+/* Enqueues one replay on `stream` (asynchronous; synchronise the stream to read the bits). */
+rmdec_status rmdec_graph_launch(rmdec_graph_t g, void *stream);
+void rmdec_graph_destroy(rmdec_graph_t g);
+
 /* Per-thread description of the last failure on this handle (or of the last failed create
  * when h is NULL). Never NULL; valid until the next call on the same handle. */
 const char *rmdec_last_error(rmdec_t h);

@@ -54,6 +54,12 @@ def load_library():
         "rmdec_submit": ([V, V, I64, V, V, ctypes.POINTER(U64)], I),
         "rmdec_poll": ([V, U64, I64], I),
         "rmdec_last_error": ([V], ctypes.c_char_p),
+        "rmdec_set_tuning": ([V, I, I], I),
+        "rmdec_get_tuning": ([V, ctypes.POINTER(I), ctypes.POINTER(I)], I),
+        "rmdec_autotune": ([V, I64, ctypes.c_char_p, V], I),
+        "rmdec_graph_create": ([V, V, I64, V, ctypes.POINTER(V)], I),
+        "rmdec_graph_launch": ([V, V], I),
+        "rmdec_graph_destroy": ([V], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -168,6 +174,23 @@ class Decoder:
                                                 out_host.data_ptr(), _stream_ptr(stream)))
         return out_host
 
+    def set_tuning(self, warps_per_cta=0, ctas_per_sm=0):
+        self._check(self._lib.rmdec_set_tuning(self._h, warps_per_cta, ctas_per_sm))
+
+    def get_tuning(self):
+        w, c = ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.rmdec_get_tuning(self._h, ctypes.byref(w), ctypes.byref(c)))
+        return w.value, c.value
+
+    def autotune(self, n_frames=16384, cache_path=None, stream=None):
+        cp = cache_path.encode() if cache_path else None
+        self._check(self._lib.rmdec_autotune(self._h, n_frames, cp, _stream_ptr(stream)))
+        return self.get_tuning()
+
+    def graph(self, llr_host, out_host):
+        """A captured host-to-host decode (H2D, decode, D2H) for these fixed CPU buffers."""
+        return Graph(self, llr_host, out_host)
+
     def submit(self, llr, out, stream=None):
         t = ctypes.c_uint64()
         self._check(self._lib.rmdec_submit(self._h, _ptr(llr), llr.shape[0], _ptr(out), _stream_ptr(stream),
@@ -180,6 +203,33 @@ class Decoder:
         if st in (OK, EBUSY, ETIMEDOUT):
             return st
         return self._check(st)
+
+
+class Graph:
+    """rmdec_graph_t: one replay = H2D of the LLRs, decode, D2H of the bits."""
+
+    def __init__(self, dec, llr_host, out_host):
+        self._dec = dec
+        self._lib = dec._lib
+        self._bufs = (llr_host, out_host)  # the host buffers must outlive the graph
+        g = ctypes.c_void_p()
+        dec._check(self._lib.rmdec_graph_create(dec._h, llr_host.data_ptr(), llr_host.shape[0],
+                                                out_host.data_ptr(), ctypes.byref(g)))
+        self._g = g
+
+    def launch(self, stream=None):
+        self._dec._check(self._lib.rmdec_graph_launch(self._g, _stream_ptr(stream)))
+
+    def close(self):
+        if getattr(self, "_g", None):
+            self._lib.rmdec_graph_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def unpack_bits(words, nbits):

@@ -12,6 +12,7 @@
 #include <thread>
 #include <vector>
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "../../include/rmdec.h"
@@ -127,6 +128,8 @@ struct rmdec_ctx {
     uint16_t* d_info = nullptr;
     rmdec_host::KernelEntry kern;
     int warps = 4;
+    int req_warps = 0, req_ctas = 0;  // requested launch shape (0 = default)
+    bool shape_dirty = true;
     int sm_count = 0;
     int blocks_per_sm = 0;
     size_t smem = 0;
@@ -222,23 +225,36 @@ rmdec_status ensure_device(rmdec_ctx* h) {
     std::vector<uint16_t> info16(h->info.begin(), h->info.end());
     if ((e = cudaMemcpy(h->d_recs, recs.data(), recs.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess) return h->cuda_fail(e, "upload records");
     if ((e = cudaMemcpy(h->d_info, info16.data(), info16.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess) return h->cuda_fail(e, "upload info");
-    // warps per CTA: decoders of one frame split across warps
-    int W = h->algo == 0 ? std::min(h->P, 4) : 4;
-    if (const char* s = getenv("RMDEC_WARPS")) W = std::max(1, std::min(4, atoi(s)));
+    h->shape_dirty = true;
+    h->device = dev;
+    h->dirty = false;
+    return RMDEC_OK;
+}
+
+// Launch shape: warps per CTA (decoders of a frame split across warps) and resident CTAs.
+rmdec_status configure_shape(rmdec_ctx* h) {
+    if (!h->shape_dirty) return RMDEC_OK;
+    cudaError_t e;
+    int W = h->req_warps ? h->req_warps : (h->algo == 0 ? std::min(h->P, 4) : 4);
+    if (!h->req_warps)
+        if (const char* s = getenv("RMDEC_WARPS")) W = atoi(s);
+    W = std::max(1, std::min(4, W));
+    if (h->algo == 0) W = std::min(W, h->P);
     h->warps = W;
     h->smem = (size_t)h->kern.fixed_bytes(h->P, h->k, W) + 16 + (size_t)W * h->kern.warp_bytes;
     int max_optin = 0;
-    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
     if ((int)h->smem > max_optin) return h->fail(RMDEC_EINVAL, "configuration needs %zu B shared memory (max %d)", h->smem, max_optin);
     // permit the device maximum so that handles of different sizes sharing this kernel can
     // launch in any order
     if ((e = cudaFuncSetAttribute(h->kern.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)) != cudaSuccess)
         return h->cuda_fail(e, "cudaFuncSetAttribute");
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->blocks_per_sm, h->kern.fn, 32 * W, h->smem)) != cudaSuccess)
+    int occ = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, h->kern.fn, 32 * W, h->smem)) != cudaSuccess)
         return h->cuda_fail(e, "occupancy");
-    if (h->blocks_per_sm < 1) return h->fail(RMDEC_EINVAL, "kernel cannot be resident (smem %zu)", h->smem);
-    h->device = dev;
-    h->dirty = false;
+    if (occ < 1) return h->fail(RMDEC_EINVAL, "kernel cannot be resident (smem %zu)", h->smem);
+    h->blocks_per_sm = h->req_ctas ? std::min(h->req_ctas, occ) : occ;
+    h->shape_dirty = false;
     return RMDEC_OK;
 }
 
@@ -249,6 +265,7 @@ rmdec_status launch(rmdec_ctx* h, const void* llr, int64_t n_frames, uint32_t* b
     if (!llr || !bits) return h->fail(RMDEC_EINVAL, "null llr or output pointer");
     if (reinterpret_cast<uintptr_t>(llr) % 16) return h->fail(RMDEC_EINVAL, "llr buffer must be 16-byte aligned");
     rmdec_status st = ensure_device(h);
+    if (st == RMDEC_OK) st = configure_shape(h);
     if (st != RMDEC_OK) return st;
     rmdec_dev::LaunchArgs a;
     a.llr = llr;
@@ -464,6 +481,193 @@ rmdec_status rmdec_poll(rmdec_t h, uint64_t ticket, int64_t timeout_us) {
         if (us >= timeout_us) return h->fail(RMDEC_ETIMEDOUT, "ticket %llu not finished after %lld us", (unsigned long long)ticket, (long long)timeout_us);
         std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
+}
+
+rmdec_status rmdec_set_tuning(rmdec_t h, int warps_per_cta, int ctas_per_sm) {
+    if (!h) return RMDEC_EINVAL;
+    if (warps_per_cta < 0 || warps_per_cta > 4 || ctas_per_sm < 0 || ctas_per_sm > 32)
+        return h->fail(RMDEC_EINVAL, "warps_per_cta must be 0..4 and ctas_per_sm 0..32");
+    h->req_warps = warps_per_cta;
+    h->req_ctas = ctas_per_sm;
+    h->shape_dirty = true;
+    return RMDEC_OK;
+}
+
+rmdec_status rmdec_get_tuning(rmdec_t h, int* warps_per_cta, int* ctas_per_sm) {
+    if (!h) return RMDEC_EINVAL;
+    rmdec_status st = ensure_device(h);
+    if (st == RMDEC_OK) st = configure_shape(h);
+    if (st != RMDEC_OK) return st;
+    if (warps_per_cta) *warps_per_cta = h->warps;
+    if (ctas_per_sm) *ctas_per_sm = h->blocks_per_sm;
+    return RMDEC_OK;
+}
+
+rmdec_status rmdec_autotune(rmdec_t h, int64_t n_frames, const char* cache_path, void* stream) {
+    if (!h) return RMDEC_EINVAL;
+    if (n_frames < 1) return h->fail(RMDEC_EINVAL, "n_frames must be positive");
+    rmdec_status st = ensure_device(h);
+    if (st != RMDEC_OK) return st;
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, h->device);
+    char key[512];
+    snprintf(key, sizeof key, "%.200s|algo%d|m%d|r%d|P%d|L%d|dt%d", prop.name, h->algo, h->m, h->r, h->P, h->L,
+             (int)h->dtype);
+    for (char* c = key; *c; c++)
+        if (*c == ' ') *c = '_';
+    if (cache_path) {
+        if (FILE* f = fopen(cache_path, "r")) {
+            // one "key warps ctas" entry per line; the last entry for this key wins
+            char k[512];
+            int w = 0, c = 0, found = 0, fw = 0, fc = 0;
+            while (fscanf(f, "%511s %d %d", k, &w, &c) == 3)
+                if (!strcmp(k, key)) {
+                    found = 1;
+                    fw = w;
+                    fc = c;
+                }
+            fclose(f);
+            if (found) {
+                h->req_warps = std::max(0, std::min(4, fw));
+                h->req_ctas = std::max(0, std::min(32, fc));
+                h->shape_dirty = true;
+                return configure_shape(h);
+            }
+        }
+    }
+    // synthetic frames: BPSK-like LLRs (+-2 plus uniform noise) from a fixed xorshift stream
+    const size_t eb = llr_elem_bytes(h->dtype);
+    const size_t in_b = (size_t)n_frames * h->n * eb, out_b = (size_t)n_frames * ((h->k + 31) / 32) * 4;
+    std::vector<uint8_t> host(in_b);
+    uint64_t x = 0x9E3779B97F4A7C15ull;
+    for (size_t i = 0; i < (size_t)n_frames * h->n; i++) {
+        x ^= x << 13;
+        x ^= x >> 7;
+        x ^= x << 17;
+        const float v = ((x & 1) ? 2.f : -2.f) + (float)((x >> 11) % 4096) / 1024.f - 2.f;
+        if (h->dtype == RMDEC_LLR_F32) memcpy(&host[i * 4], &v, 4);
+        else if (h->dtype == RMDEC_LLR_I8) host[i] = (uint8_t)(int8_t)(v * 4.f);
+        else if (h->dtype == RMDEC_LLR_I16) {
+            const int16_t q = (int16_t)(v * 256.f);
+            memcpy(&host[i * 2], &q, 2);
+        } else {
+            const __half hv = __float2half(v);
+            memcpy(&host[i * 2], &hv, 2);
+        }
+    }
+    void* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, in_b + out_b + 256);
+    if (e != cudaSuccess) return h->fail(RMDEC_ENOMEM, "autotune buffers: %s", cudaGetErrorString(e));
+    cudaStream_t s = (cudaStream_t)stream;
+    uint8_t* din = static_cast<uint8_t*>(d);
+    uint32_t* dout = reinterpret_cast<uint32_t*>(din + (in_b + 255) / 256 * 256);
+    cudaMemcpy(din, host.data(), in_b, cudaMemcpyHostToDevice);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    int best_w = 0;
+    const int wmax = h->algo == 0 ? std::min(4, h->P) : 4;
+    for (int w = 1; w <= wmax; w *= 2) {
+        h->req_warps = w;
+        h->req_ctas = 0;
+        h->shape_dirty = true;
+        if (configure_shape(h) != RMDEC_OK) continue;
+        launch(h, din, n_frames, dout, nullptr, nullptr, nullptr, s);  // warm-up
+        cudaEventRecord(e0, s);
+        for (int rep = 0; rep < 3; rep++) launch(h, din, n_frames, dout, nullptr, nullptr, nullptr, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_w = w;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d);
+    if ((e = cudaGetLastError()) != cudaSuccess) return h->cuda_fail(e, "autotune");
+    if (!best_w) return h->fail(RMDEC_EINVAL, "no launch shape fits");
+    h->req_warps = best_w;
+    h->req_ctas = 0;
+    h->shape_dirty = true;
+    st = configure_shape(h);
+    if (st == RMDEC_OK && cache_path) {
+        if (FILE* f = fopen(cache_path, "a")) {
+            fprintf(f, "%s %d %d\n", key, best_w, 0);
+            fclose(f);
+        }
+    }
+    return st;
+}
+
+}  // extern "C"
+
+struct rmdec_graph {
+    rmdec_ctx* h = nullptr;
+    void* dbuf = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+rmdec_status rmdec_graph_create(rmdec_t h, const void* llr_host, int64_t n_frames, uint32_t* bits_out_host,
+                                rmdec_graph_t* out) {
+    if (!h || !out) return RMDEC_EINVAL;
+    *out = nullptr;
+    if (n_frames < 1 || !llr_host || !bits_out_host) return h->fail(RMDEC_EINVAL, "bad graph buffers");
+    rmdec_status st = ensure_device(h);
+    if (st == RMDEC_OK) st = configure_shape(h);
+    if (st != RMDEC_OK) return st;
+    rmdec_graph* g = new (std::nothrow) rmdec_graph;
+    if (!g) return RMDEC_ENOMEM;
+    g->h = h;
+    const size_t in_b = (size_t)n_frames * h->n * llr_elem_bytes(h->dtype), in_pad = (in_b + 255) / 256 * 256;
+    const size_t out_b = (size_t)n_frames * ((h->k + 31) / 32) * 4;
+    cudaError_t e = cudaMalloc(&g->dbuf, in_pad + out_b);
+    if (e != cudaSuccess) {
+        delete g;
+        return h->fail(RMDEC_ENOMEM, "graph buffers: %s", cudaGetErrorString(e));
+    }
+    uint8_t* din = static_cast<uint8_t*>(g->dbuf);
+    uint32_t* dout = reinterpret_cast<uint32_t*>(din + in_pad);
+    cudaStream_t cs;
+    cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaMemcpyAsync(din, llr_host, in_b, cudaMemcpyHostToDevice, cs);
+        st = launch(h, din, n_frames, dout, nullptr, nullptr, nullptr, cs);
+        cudaMemcpyAsync(bits_out_host, dout, out_b, cudaMemcpyDeviceToHost, cs);
+        e = cudaStreamEndCapture(cs, &g->graph);
+    }
+    if (e == cudaSuccess && st == RMDEC_OK) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess || st != RMDEC_OK) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        cudaFree(g->dbuf);
+        delete g;
+        return st != RMDEC_OK ? st : h->cuda_fail(e, "graph capture");
+    }
+    *out = g;
+    return RMDEC_OK;
+}
+
+rmdec_status rmdec_graph_launch(rmdec_graph_t g, void* stream) {
+    if (!g) return RMDEC_EINVAL;
+    const cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+    return e == cudaSuccess ? RMDEC_OK : g->h->cuda_fail(e, "graph launch");
+}
+
+void rmdec_graph_destroy(rmdec_graph_t g) {
+    if (!g) return;
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+    cudaFree(g->dbuf);
+    delete g;
 }
 
 const char* rmdec_last_error(rmdec_t h) {

@@ -1,0 +1,70 @@
+"""Launch-shape tuning, the autotuner's cache and captured CUDA graphs: none of them may change
+a single decoded bit."""
+import os
+
+import numpy as np
+import pytest
+
+import paper_2108_12550_gb300 as pkg
+from paper_2108_12550_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+
+
+def test_tuning_arguments_are_validated():
+    d = pkg.Decoder(9, 2, 20, 4)
+    for bad in [(5, 0), (-1, 0), (2, 33)]:
+        with pytest.raises(pkg.RmdecError):
+            d.set_tuning(*bad)
+    d.set_tuning(2, 1)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("m,r,P,L", [(9, 2, 20, 4), (9, 3, 16, 8), (5, 2, 4, 2)])
+def test_every_launch_shape_gives_identical_results(m, r, P, L):
+    fr = I.make_frames(m, r, 1000, 2.5, seed=4)
+    x = torch.from_numpy(fr["llr"].astype(np.float32)).cuda()
+    d = pkg.Decoder(m, r, P, L, perm_seed=3)
+    outs = []
+    for w in (1, 2, 4):
+        for c in (0, 1):
+            d.set_tuning(w, c)
+            outs.append(d.decode(x).cpu())
+            assert d.get_tuning()[0] == min(w, P)
+    assert all(torch.equal(o, outs[0]) for o in outs)
+
+
+@pytest.mark.gpu
+def test_autotune_and_cache(tmp_path):
+    cache = str(tmp_path / "tune.txt")
+    d = pkg.Decoder(9, 2, 20, 4, perm_seed=1)
+    w, c = d.autotune(n_frames=8192, cache_path=cache)
+    assert 1 <= w <= 4 and c >= 1
+    lines = open(cache).read().split("\n")
+    assert len([l for l in lines if l.strip()]) == 1
+    d2 = pkg.Decoder(9, 2, 20, 4, perm_seed=2)
+    assert d2.autotune(n_frames=8192, cache_path=cache)[0] == w  # reused, not re-timed
+    assert len([l for l in open(cache).read().split("\n") if l.strip()]) == 1
+
+
+@pytest.mark.gpu
+def test_graph_replays_match_direct_decoding():
+    m, r, P, L = 7, 2, 8, 4
+    d = pkg.Decoder(m, r, P, L, perm_seed=6)
+    fr = I.make_frames(m, r, 777, 2.0, seed=8)
+    host_in = torch.from_numpy(fr["llr"].astype(np.float32)).pin_memory()
+    host_out = torch.zeros((777, d.kw), dtype=torch.int32).pin_memory()
+    ref = d.decode(host_in.cuda()).cpu()
+    g = d.graph(host_in, host_out)
+    for _ in range(3):
+        host_out.zero_()
+        g.launch()
+        torch.cuda.synchronize()
+        assert torch.equal(host_out, ref)
+    # new LLRs in the same host buffer are picked up by the next replay
+    fr2 = I.make_frames(m, r, 777, 2.0, seed=9)
+    host_in.copy_(torch.from_numpy(fr2["llr"].astype(np.float32)))
+    g.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(host_out, d.decode(host_in.cuda()).cpu())
+    g.close()
