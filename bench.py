@@ -237,13 +237,70 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+# Frame error rates printed in the paper's Fig. 6 (RM(2,9) panel) for comparison
+PAPER_FER = {"p-FHT-FSCL-4-20": {1.0: 9.80e-3, 1.5: 2.11e-3, 2.0: 2.99e-4, 2.5: 2.85e-5},
+             "Aut-SSC-512": {1.0: 9.38e-3, 1.5: 2.14e-3, 2.0: 2.58e-4, 2.5: 2.76e-5}}
+
+
+def run_fer_sweep(args):
+    """FER of p-FHT-FSCL-4-20 and Aut-SSC-512 on the same RM(2,9) frames, generated on the GPU
+    in chunks, with decoding time per point."""
+    import torch
+
+    import paper_2108_12550_gb300 as pkg
+
+    m, r, k = 9, 2, 46
+    pf = pkg.Decoder(m, r, 20, 4, perm_seed=1)
+    ssc = pkg.Decoder(m, r, 512, algo="autssc", perm_seed=1)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(2108)
+    chunk = 1 << 18
+    out = torch.empty((chunk, 2), dtype=torch.int32, device="cuda")
+    points = []
+    for eb in args.ebn0:
+        n_pf = args.sweep_frames
+        n_ssc = min(args.sweep_frames, args.ssc_frames)
+        err = {"p-FHT-FSCL-4-20": 0, "Aut-SSC-512": 0}
+        t_dec = {"p-FHT-FSCL-4-20": 0.0, "Aut-SSC-512": 0.0}
+        done = 0
+        while done < n_pf:
+            f = min(chunk, n_pf - done)
+            u, llr = I.make_frames_torch(m, r, f, eb, gen)
+            unpack = lambda w: ((w.view(-1, 2, 1) >> torch.arange(32, device="cuda")) & 1).view(-1, 64)[:, :k]
+            for name, dec, lim in (("p-FHT-FSCL-4-20", pf, n_pf), ("Aut-SSC-512", ssc, n_ssc)):
+                if done >= lim:
+                    continue
+                g = min(f, lim - done)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                dec.decode(llr[:g], out[:g])
+                e1.record()
+                torch.cuda.synchronize()
+                t_dec[name] += e0.elapsed_time(e1) * 1e-3
+                err[name] += int(torch.any(unpack(out[:g]).to(torch.uint8) != u[:g], dim=1).sum().item())
+            done += f
+        pt = {"ebn0_db": eb}
+        for name, n in (("p-FHT-FSCL-4-20", n_pf), ("Aut-SSC-512", n_ssc)):
+            pt[name] = {"frames": n, "errors": err[name], "fer": err[name] / n,
+                        "frames_per_s": n / t_dec[name] if t_dec[name] else None,
+                        "paper_fer": PAPER_FER[name].get(eb)}
+        points.append(pt)
+        print(json.dumps(pt), flush=True)
+    print(json.dumps({"metric": "FER RM(2,9): p-FHT-FSCL-4-20 vs Aut-SSC-512 on the same frames", "points": points,
+                      "data": "synthetic BPSK/AWGN frames generated on the GPU"}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="rm29_p20_l4", choices=sorted(WORKLOADS) + ["serving_mix"])
+    ap.add_argument("--workload", default="rm29_p20_l4", choices=sorted(WORKLOADS) + ["serving_mix", "fer_sweep"])
+    ap.add_argument("--ebn0", type=float, nargs="+", default=[1.0, 1.5, 2.0, 2.25, 2.5],
+                    help="FER sweep: Eb/N0 points (dB)")
+    ap.add_argument("--sweep-frames", type=int, default=1 << 22, help="FER sweep: frames per point")
+    ap.add_argument("--ssc-frames", type=int, default=1 << 20, help="FER sweep: Aut-SSC frames per point")
     ap.add_argument("--requests", type=int, default=2000, help="serving mix: requests in the trace")
     ap.add_argument("--rate", type=float, default=8000.0, help="serving mix: Poisson arrivals per second")
     ap.add_argument("--streams", type=int, default=4, help="serving mix: server CUDA streams")
@@ -255,6 +312,8 @@ def main():
     args = ap.parse_args()
     if args.workload == "serving_mix":
         return run_serving(args)
+    if args.workload == "fer_sweep":
+        return run_fer_sweep(args)
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl)

@@ -211,3 +211,23 @@ SSC_STREAM = 0x53534300  # counter word 0 of the Aut-SSC permutation draws
 def ssc_perm_table(m: int, P_ssc: int, seed: int) -> np.ndarray:
     """(P_ssc, 11) uint16 GA(m) records for the Aut-SSC-P baseline (counter word 0 = 'SSC\\0')."""
     return np.stack([sample_ga(m, seed, SSC_STREAM, q) for q in range(P_ssc)])
+
+
+def make_frames_torch(m: int, r: int, n_frames: int, ebn0_db: float, generator, device="cuda"):
+    """The same transmitter and channel as make_frames, on a torch device (for sweeps whose
+    frames are too many to stage from the host): uniform messages, x = u G^{(x)m}, BPSK over
+    AWGN, FP32 LLRs 2y/sigma^2. Returns (u uint8 [F,K], llr float32 [F,N])."""
+    import torch
+
+    n, k = rm_dims(m, r)
+    u = torch.randint(0, 2, (n_frames, k), dtype=torch.uint8, device=device, generator=generator)
+    x = torch.zeros((n_frames, n), dtype=torch.uint8, device=device)
+    x[:, torch.as_tensor(info_set(m, r), device=device)] = u
+    for t in range(m):
+        h = 1 << t
+        v = x.view(n_frames, n // (2 * h), 2, h)
+        v[:, :, 0, :] ^= v[:, :, 1, :]
+    s2 = sigma2_for(ebn0_db, m, r)
+    z = torch.randn((n_frames, n), dtype=torch.float32, device=device, generator=generator)
+    y = (1.0 - 2.0 * x.float()) + math.sqrt(s2) * z
+    return u, (2.0 / s2) * y

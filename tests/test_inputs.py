@@ -111,3 +111,14 @@ def test_channel_and_quantisers():
     assert q.tolist() == [0, 2, 0, 127, -127, 1]  # half to even, saturate at +-127
     nl = I.noiseless_frames(5, 2, 4, seed=1)
     assert np.all((nl["llr"] < 0) == (nl["x"] == 1))
+
+
+def test_torch_frame_generator_encodes_like_numpy():
+    torch = pytest.importorskip("torch")
+    g = torch.Generator()
+    g.manual_seed(3)
+    for m, r in [(5, 2), (9, 3)]:
+        u, llr = I.make_frames_torch(m, r, 50, 40.0, g, device="cpu")  # 40 dB: signs are the codeword
+        x = I.encode(u.numpy(), m, r)
+        assert np.array_equal((llr.numpy() < 0).astype(np.uint8), x)
+        assert llr.dtype == torch.float32
