@@ -50,7 +50,8 @@ typedef enum {
 
 /* Creates a p-FHT-FSCL-L-P decoder for RM(r, m) (Algorithm 5 with Algorithm 2 per decoder).
  * Supported: 4 <= m <= 9, r in {2, 3} with r <= m - 2 (the root is a permuted node,
- * 1 < r < m - 1), 1 <= P <= 64, L in {1, 2, 4, 8}.
+ * 1 < r < m - 1), 1 <= P <= 128, L in {1, 2, 4, 8} (P = M_1 = 100, L = 1 is the paper's
+ * p-FHT-FSCL-1-100).
  * The affine permutations x -> Ax + b of GA(m) that Algorithm 2 draws (L initial ones and
  * 2L candidates at each of the r - 1 permuted nodes, per decoder) are sampled on the host
  * from perm_seed with Philox4x32-10 (counter (p, q, attempt, 'PERM'), key = perm_seed) and
@@ -58,6 +59,12 @@ typedef enum {
  * No GPU work happens here: device state is built on the first decode.
  * *out receives the handle (NULL on failure). */
 rmdec_status rmdec_create(rmdec_t *out, int m, int r, int P, int L, uint64_t perm_seed);
+
+/* Creates an FHT-FSCL-L decoder: the same tree without permutations, started from a single
+ * live path (the decoder the paper's permuted decoder improves on; its Fig. 4 dashed curves).
+ * Equivalent to p-FHT-FSCL-L-1 with identity permutations whose paths 1..L-1 start inactive.
+ * Same support limits as rmdec_create with P = 1; the permutation table is fixed (identity). */
+rmdec_status rmdec_create_fhtfscl(rmdec_t *out, int m, int r, int L);
 
 /* Creates an Aut-SSC-P baseline decoder (the permuted simplified SC decoder the paper
  * compares against, Section III-B, Table 5): SSC decoding (repetition, SPC and f/g nodes,

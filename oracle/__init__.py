@@ -58,6 +58,8 @@ def _load():
         for name in ("rmo_fhtl_f64", "rmo_spcl_f64"):
             getattr(lib, name).argtypes = [i, i, P, P, P, P, P]
             getattr(lib, name).restype = i
+        lib.rmo_decode_fhtfscl.argtypes = [i, i, i, i, P, i64, i, P, P, P, P]
+        lib.rmo_decode_fhtfscl.restype = i
         lib.rmo_fht_f64.argtypes = [P, i]
         lib.rmo_fht_f64.restype = None
         _lib = lib
@@ -102,6 +104,27 @@ def decode(m, r, P, L, perms, llr, integer=False, n_threads=0, want_margin=True,
     if rc != 0:
         raise RuntimeError(f"oracle decode failed rc={rc}")
     return {"cw": cw, "info": info, "pm": pm, "margin": margin, "ops": ops, "best": best}
+
+
+def decode_fhtfscl(m, r, L, llr, integer=False, n_threads=0):
+    """FHT-FSCL-L: the recursion without permutations from one live initial path."""
+    lib = _load()
+    n = 1 << m
+    if integer:
+        y = np.ascontiguousarray(llr, dtype=np.int64).reshape(-1, n)
+        pm = np.zeros(y.shape[0], dtype=np.int64)
+    else:
+        y = np.ascontiguousarray(llr, dtype=np.float64).reshape(-1, n)
+        pm = np.zeros(y.shape[0], dtype=np.float64)
+    F = y.shape[0]
+    cw = np.zeros((F, n), dtype=np.uint8)
+    info = np.zeros((F, _k(m, r)), dtype=np.uint8)
+    margin = np.zeros(F, dtype=np.float64)
+    rc = lib.rmo_decode_fhtfscl(m, r, L, 1 if integer else 0, _ptr(y), F, n_threads, _ptr(cw), _ptr(info),
+                                _ptr(pm), _ptr(margin))
+    if rc != 0:
+        raise RuntimeError(f"oracle FHT-FSCL decode failed rc={rc}")
+    return {"cw": cw, "info": info, "pm": pm, "margin": margin}
 
 
 def aut_ssc(m, r, perms, llr, integer=False, n_threads=0):

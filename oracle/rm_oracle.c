@@ -85,6 +85,7 @@ static int extract_info(const uint8_t *cw, int m, int r, uint8_t *info) {
 typedef struct {
     int kind; /* 0 f64 decode, 1 i64 decode, 2 f64 aut-ssc, 3 i64 aut-ssc */
     int m, r, P, L;
+    int no_perm; /* FHT-FSCL (no permutations) */
     const uint16_t *perms;
     const void *llr;
     int64_t f0, f1;
@@ -109,12 +110,12 @@ static void *run_job(void *arg) {
         int best = -1;
         if (j->kind == 0) {
             const double *y = (const double *)j->llr + f * N;
-            best = decode_frame_f64(j->m, j->r, j->P, j->L, j->perms, y, ba, bb, cw,
+            best = decode_frame_f64(j->m, j->r, j->P, j->L, j->no_perm, j->perms, y, ba, bb, cw,
                                     (double *)j->pm_out + f, j->margin_out ? j->margin_out + f : NULL,
                                     j->ops_out ? j->ops_out + f : NULL);
         } else if (j->kind == 1) {
             const int64_t *y = (const int64_t *)j->llr + f * N;
-            best = decode_frame_i64(j->m, j->r, j->P, j->L, j->perms, y, ba, bb, cw,
+            best = decode_frame_i64(j->m, j->r, j->P, j->L, j->no_perm, j->perms, y, ba, bb, cw,
                                     (int64_t *)j->pm_out + f, j->margin_out ? j->margin_out + f : NULL,
                                     j->ops_out ? j->ops_out + f : NULL);
         } else if (j->kind == 2) {
@@ -162,7 +163,16 @@ static int run_batch(job_t proto, int64_t n_frames, int n_threads) {
 int rmo_decode_f64(int m, int r, int P, int L, const uint16_t *perms, const double *llr,
                    int64_t n_frames, int n_threads, uint8_t *cw_out, uint8_t *info_out,
                    double *pm_out, double *margin_out, int64_t *ops_out, int32_t *best_out) {
-    job_t j = {0, m, r, P, L, perms, llr, 0, 0, cw_out, info_out, pm_out, margin_out, ops_out, best_out, 0};
+    job_t j = {0, m, r, P, L, 0, perms, llr, 0, 0, cw_out, info_out, pm_out, margin_out, ops_out, best_out, 0};
+    return run_batch(j, n_frames, n_threads);
+}
+
+/* FHT-FSCL-L: the same recursion without permutations, starting from one live path (the
+ * decoder the paper's p-FHT-FSCL improves on, its Fig. 4 dashed curves); P = 1. integer
+ * selects the int64 mode (llr then points to int64 values, pm_out to int64). */
+int rmo_decode_fhtfscl(int m, int r, int L, int integer, const void *llr, int64_t n_frames, int n_threads,
+                       uint8_t *cw_out, uint8_t *info_out, void *pm_out, double *margin_out) {
+    job_t j = {integer ? 1 : 0, m, r, 1, L, 1, NULL, llr, 0, 0, cw_out, info_out, pm_out, margin_out, NULL, NULL, 0};
     return run_batch(j, n_frames, n_threads);
 }
 
@@ -170,7 +180,7 @@ int rmo_decode_f64(int m, int r, int P, int L, const uint16_t *perms, const doub
 int rmo_decode_i64(int m, int r, int P, int L, const uint16_t *perms, const int64_t *llr,
                    int64_t n_frames, int n_threads, uint8_t *cw_out, uint8_t *info_out,
                    int64_t *pm_out, double *margin_out, int64_t *ops_out, int32_t *best_out) {
-    job_t j = {1, m, r, P, L, perms, llr, 0, 0, cw_out, info_out, pm_out, margin_out, ops_out, best_out, 0};
+    job_t j = {1, m, r, P, L, 0, perms, llr, 0, 0, cw_out, info_out, pm_out, margin_out, ops_out, best_out, 0};
     return run_batch(j, n_frames, n_threads);
 }
 
@@ -179,14 +189,14 @@ int rmo_decode_i64(int m, int r, int P, int L, const uint16_t *perms, const int6
 int rmo_aut_ssc_f64(int m, int r, int Pssc, const uint16_t *perms, const double *llr,
                     int64_t n_frames, int n_threads, uint8_t *cw_out, uint8_t *info_out,
                     double *disc_out, int32_t *best_out) {
-    job_t j = {2, m, r, Pssc, 1, perms, llr, 0, 0, cw_out, info_out, disc_out, NULL, NULL, best_out, 0};
+    job_t j = {2, m, r, Pssc, 1, 0, perms, llr, 0, 0, cw_out, info_out, disc_out, NULL, NULL, best_out, 0};
     return run_batch(j, n_frames, n_threads);
 }
 
 int rmo_aut_ssc_i64(int m, int r, int Pssc, const uint16_t *perms, const int64_t *llr,
                     int64_t n_frames, int n_threads, uint8_t *cw_out, uint8_t *info_out,
                     int64_t *disc_out, int32_t *best_out) {
-    job_t j = {3, m, r, Pssc, 1, perms, llr, 0, 0, cw_out, info_out, disc_out, NULL, NULL, best_out, 0};
+    job_t j = {3, m, r, Pssc, 1, 0, perms, llr, 0, 0, cw_out, info_out, disc_out, NULL, NULL, best_out, 0};
     return run_batch(j, n_frames, n_threads);
 }
 

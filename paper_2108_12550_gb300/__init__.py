@@ -42,6 +42,7 @@ def load_library():
     sig = {
         "rmdec_create": ([ctypes.POINTER(V), I, I, I, I, U64], I),
         "rmdec_create_aut_ssc": ([ctypes.POINTER(V), I, I, I, U64], I),
+        "rmdec_create_fhtfscl": ([ctypes.POINTER(V), I, I, I], I),
         "rmdec_destroy": ([V], None),
         "rmdec_set_dtype": ([V, I], I),
         "rmdec_perm_count": ([V, ctypes.POINTER(I64)], I),
@@ -81,7 +82,8 @@ def _ptr(t):
 
 
 class Decoder:
-    """A decoder handle. algo='pfht' (p-FHT-FSCL-L-P, Algorithm 5) or 'autssc' (Aut-SSC-P)."""
+    """A decoder handle. algo='pfht' (p-FHT-FSCL-L-P, Algorithm 5), 'fhtfscl' (FHT-FSCL-L, no
+    permutations; P must be 1) or 'autssc' (Aut-SSC-P)."""
 
     def __init__(self, m, r, P, L=1, perm_seed=0, dtype="f32", perms=None, algo="pfht"):
         lib = load_library()
@@ -91,12 +93,14 @@ class Decoder:
             st = lib.rmdec_create(ctypes.byref(h), m, r, P, L, perm_seed)
         elif algo == "autssc":
             st = lib.rmdec_create_aut_ssc(ctypes.byref(h), m, r, P, perm_seed)
+        elif algo == "fhtfscl":
+            st = lib.rmdec_create_fhtfscl(ctypes.byref(h), m, r, L)
         else:
             raise ValueError(algo)
         if st != OK:
             raise RmdecError(st, lib.rmdec_last_error(None).decode())
         self._h = h
-        self.m, self.r, self.P, self.L, self.algo = m, r, P, (L if algo == "pfht" else 1), algo
+        self.m, self.r, self.P, self.L, self.algo = m, r, P, (1 if algo == "autssc" else L), algo
         n, k = ctypes.c_int(), ctypes.c_int()
         idx = ctypes.POINTER(ctypes.c_int)()
         self._check(lib.rmdec_info(h, ctypes.byref(n), ctypes.byref(k), ctypes.byref(idx)))

@@ -47,6 +47,7 @@ struct LaunchArgs {
     uint32_t* cw_out;    // [F][ceil(N/32)] or null
     float* pm_out;       // [F] or null
     int32_t* best_out;   // [F] or null
+    int single_start;    // one live initial path (FHT-FSCL without permutations)
 };
 
 // Shared-memory layout of one decoder configuration.
@@ -99,6 +100,7 @@ struct Warp {
     const uint16_t* rec;  // this decoder's NREC records
     int lane;
     int bsel;           // current bit buffer (warp uniform)
+    bool single;        // paths 1..L-1 start inactive (metric +inf)
 };
 
 template <int M>
@@ -588,12 +590,13 @@ struct Decoder {
                 // composed permutation pi^init_{c mod L} o pi_c (one GA(m) element)
                 const int c = select_perms<S>(w, lrec, [&](int, int j) { return w.y[j]; });
                 ps.rootc = c;
-                ps.pm = 0.f;
+                ps.pm = __shfl_sync(kFull, ps.pm, c & (L - 1));  // the source path's start metric
             } else if constexpr (PERM) {
                 const float* src = w.alpha + C::lvl_off(S);
                 const int c = select_perms<S>(w, lrec, [&](int l, int j) { return src[l * STN + j]; });
                 // path q takes source path c mod L through pi_c
-                reselect<OFF, PEND>(w, ps, c % L, ps.pm);
+                const float npm = __shfl_sync(kFull, ps.pm, (w.lane < L ? c : 0) & (L - 1));
+                reselect<OFF, PEND>(w, ps, c % L, npm);
                 ps.selc[S] = c;
                 float* dst = w.alpha + C::alt_off(S);
 #pragma unroll 1
@@ -766,7 +769,7 @@ struct Decoder {
     // root permutation. The path's bits stay in its bit buffer (see emit()).
     __device__ static float run(Warp& w, int& c0) {
         PState<M> ps;
-        ps.pm = 0.f;
+        ps.pm = (w.single && w.lane != 0) ? __int_as_float(0x7f800000) : 0.f;
         ps.rootc = 0;
 #pragma unroll
         for (int s = 0; s <= M; s++) {
@@ -835,6 +838,7 @@ __global__ void __launch_bounds__(128, 4) pfht_kernel(LaunchArgs args) {
     w.spc = mine + C::OFF_SPC;
     w.y = s_y;
     w.lane = lane;
+    w.single = args.single_start != 0;
 
     for (int i = threadIdx.x; i < P * C::NREC * kRec; i += blockDim.x) s_rec[i] = args.recs[i];
     for (int i = threadIdx.x; i < K; i += blockDim.x) s_info[i] = args.info[i];

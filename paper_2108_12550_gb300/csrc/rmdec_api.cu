@@ -118,6 +118,7 @@ thread_local std::string g_create_error;
 
 struct rmdec_ctx {
     int algo = 0;  // 0: p-FHT-FSCL-L-P, 1: Aut-SSC-P
+    bool single_start = false;  // FHT-FSCL: identity permutations, one live initial path
     int m = 0, r = 0, P = 0, L = 1, n = 0, k = 0;
     rmdec_dtype dtype = RMDEC_LLR_F32;
     std::vector<uint16_t> perms;  // host table in the documented layout
@@ -280,6 +281,7 @@ rmdec_status launch(rmdec_ctx* h, const void* llr, int64_t n_frames, uint32_t* b
     a.cw_out = cw;
     a.pm_out = pm;
     a.best_out = best;
+    a.single_start = h->single_start ? 1 : 0;
     const int64_t cap = (int64_t)h->sm_count * h->blocks_per_sm;
     const unsigned grid = (unsigned)std::min<int64_t>(n_frames, cap);
     void* args[] = {&a};
@@ -295,8 +297,8 @@ rmdec_status make_handle(rmdec_t* out, int algo, int m, int r, int P, int L, uin
     }
     *out = nullptr;
     if (algo == 0) {
-        if (m < 4 || m > 9 || r < 2 || r > 3 || r > m - 2 || P < 1 || P > 64 || !(L == 1 || L == 2 || L == 4 || L == 8)) {
-            g_create_error = "unsupported p-FHT-FSCL configuration (need 4<=m<=9, r in {2,3}, r<=m-2, 1<=P<=64, L in {1,2,4,8})";
+        if (m < 4 || m > 9 || r < 2 || r > 3 || r > m - 2 || P < 1 || P > 128 || !(L == 1 || L == 2 || L == 4 || L == 8)) {
+            g_create_error = "unsupported p-FHT-FSCL configuration (need 4<=m<=9, r in {2,3}, r<=m-2, 1<=P<=128, L in {1,2,4,8})";
             return RMDEC_EINVAL;
         }
     } else {
@@ -342,6 +344,20 @@ extern "C" {
 
 rmdec_status rmdec_create(rmdec_t* out, int m, int r, int P, int L, uint64_t perm_seed) {
     return make_handle(out, 0, m, r, P, L, perm_seed);
+}
+
+rmdec_status rmdec_create_fhtfscl(rmdec_t* out, int m, int r, int L) {
+    rmdec_status st = make_handle(out, 0, m, r, 1, L, 0);
+    if (st != RMDEC_OK) return st;
+    rmdec_ctx* h = *out;
+    h->single_start = true;
+    const int rpd = h->records_per_decoder();
+    for (int q = 0; q < rpd; q++) {  // identity permutations: A = I, b = 0
+        uint16_t* rec = &h->perms[(size_t)q * kRec];
+        memset(rec, 0, sizeof(uint16_t) * kRec);
+        for (int t = 0; t < h->record_size(q); t++) rec[t] = (uint16_t)(1u << t);
+    }
+    return RMDEC_OK;
 }
 
 rmdec_status rmdec_create_aut_ssc(rmdec_t* out, int m, int r, int P_ssc, uint64_t perm_seed) {

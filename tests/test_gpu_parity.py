@@ -189,3 +189,24 @@ def test_aut_ssc_bit_exact(m, r, Ps):
     info, cw, pm, best = _gpu_decode(dec, q)
     assert np.array_equal(cw, ref["cw"]) and np.array_equal(pm.astype(np.int64), ref["disc"])
     assert np.array_equal(best, ref["best"])
+
+
+@pytest.mark.parametrize("m,r,L", [(9, 2, 4), (7, 2, 8), (9, 3, 8), (5, 2, 1)])
+def test_fhtfscl_variant_bit_exact(m, r, L):
+    fr = I.make_frames(m, r, 400, 2.5, seed=61)
+    q = I.quantize_i8(fr["llr"])
+    ref = O.decode_fhtfscl(m, r, L, q.astype(np.int64), integer=True)
+    dec = pkg.Decoder(m, r, 1, L, algo="fhtfscl", dtype="i8")
+    info, cw, pm, best = _gpu_decode(dec, q)
+    assert np.array_equal(cw, ref["cw"]) and np.array_equal(pm.astype(np.int64), ref["pm"])
+
+
+def test_p100_l1_bit_exact():
+    m, r, P, L = 9, 2, 100, 1  # the paper's p-FHT-FSCL-1-100
+    fr = I.make_frames(m, r, 200, 1.5, seed=62)
+    q = I.quantize_i8(fr["llr"])
+    perms = I.perm_table(m, r, P, L, seed=8)
+    ref = O.decode(m, r, P, L, perms, q.astype(np.int64), integer=True)
+    dec = pkg.Decoder(m, r, P, L, dtype="i8", perms=perms)
+    info, cw, pm, best = _gpu_decode(dec, q)
+    assert np.array_equal(cw, ref["cw"]) and np.array_equal(best, ref["best"])

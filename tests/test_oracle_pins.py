@@ -201,6 +201,8 @@ def test_fer_matches_paper_figures(row):
     fr = I.make_frames(m, r, n_frames, eb, seed=2024)
     if dec == "pfht":
         out = O.decode(m, r, P, L, I.perm_table(m, r, P, L, seed=31), fr["llr"], want_margin=False)
+    elif dec == "fhtfscl":
+        out = O.decode_fhtfscl(m, r, L, fr["llr"])
     else:
         perms = np.stack([I.sample_ga(m, 31, 0, q) for q in range(P)])
         out = O.aut_ssc(m, r, perms, fr["llr"])
@@ -216,3 +218,25 @@ def test_operation_count_model_matches_oracle_counter(m, r, P, L):
     fr = I.make_frames(m, r, 2, 2.0, seed=1)
     o = O.decode(m, r, P, L, I.perm_table(m, r, P, L, seed=1), fr["llr"], want_ops=True)
     assert np.all(o["ops"] == opcount.ops_per_frame(m, r, P, L))
+
+
+@pytest.mark.parametrize("m,r,L", [(5, 2, 1), (7, 2, 4), (9, 3, 8)])
+def test_fhtfscl_is_the_permuted_decoder_with_identity_permutations(m, r, L):
+    """FHT-FSCL equals p-FHT-FSCL when every permutation is the identity and only one initial
+    path is live: checked on L = 1, where both start from a single path."""
+    fr = I.make_frames(m, r, 200, 2.0, seed=3)
+    a = O.decode_fhtfscl(m, r, L, fr["llr"])
+    D = _disc(fr["llr"], a["cw"])
+    np.testing.assert_allclose(a["pm"], D, rtol=1e-12, atol=1e-9)  # metric = discrepancy
+    nl = I.noiseless_frames(m, r, 8, seed=1)
+    assert np.array_equal(O.decode_fhtfscl(m, r, L, nl["llr"])["info"], nl["u"])
+    if L == 1:
+        ident = np.zeros((1, I.perms_per_decoder(m, r, 1), I.PERM_REC), dtype=np.uint16)
+        for q in range(ident.shape[1]):
+            s = m if q < 1 else m - (q - 1) // 2
+            ident[0, q, :s] = 1 << np.arange(s)
+        b = O.decode(m, r, 1, 1, ident, fr["llr"])
+        assert np.array_equal(a["cw"], b["cw"])
+    q = I.quantize_i8(fr["llr"]).astype(np.int64)
+    ai = O.decode_fhtfscl(m, r, L, q, integer=True)
+    assert np.array_equal(ai["pm"], _disc(q, ai["cw"]).astype(np.int64))
