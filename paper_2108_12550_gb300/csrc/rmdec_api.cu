@@ -236,23 +236,39 @@ rmdec_status ensure_device(rmdec_ctx* h) {
 rmdec_status configure_shape(rmdec_ctx* h) {
     if (!h->shape_dirty) return RMDEC_OK;
     cudaError_t e;
-    int W = h->req_warps ? h->req_warps : (h->algo == 0 ? std::min(h->P, 4) : 4);
-    if (!h->req_warps)
-        if (const char* s = getenv("RMDEC_WARPS")) W = atoi(s);
-    W = std::max(1, std::min(4, W));
-    if (h->algo == 0) W = std::min(W, h->P);
-    h->warps = W;
-    h->smem = (size_t)h->kern.fixed_bytes(h->P, h->k, W) + 16 + (size_t)W * h->kern.warp_bytes;
     int max_optin = 0;
     cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-    if ((int)h->smem > max_optin) return h->fail(RMDEC_EINVAL, "configuration needs %zu B shared memory (max %d)", h->smem, max_optin);
     // permit the device maximum so that handles of different sizes sharing this kernel can
     // launch in any order
     if ((e = cudaFuncSetAttribute(h->kern.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)) != cudaSuccess)
         return h->cuda_fail(e, "cudaFuncSetAttribute");
-    int occ = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, h->kern.fn, 32 * W, h->smem)) != cudaSuccess)
-        return h->cuda_fail(e, "occupancy");
+    const int wmax = h->algo == 0 ? std::min(h->P, 4) : 4;
+    auto smem_for = [&](int W) { return (size_t)h->kern.fixed_bytes(h->P, h->k, W) + 16 + (size_t)W * h->kern.warp_bytes; };
+    auto occ_for = [&](int W) {
+        int o = 0;
+        if (smem_for(W) > (size_t)max_optin) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, h->kern.fn, 32 * W, smem_for(W)) != cudaSuccess) return 0;
+        return o;
+    };
+    int W = h->req_warps;
+    if (!W)
+        if (const char* s = getenv("RMDEC_WARPS")) W = atoi(s);
+    if (!W) {
+        // default: the most resident warps per SM, then the widest CTA
+        int best = -1;
+        for (int c = 1; c <= wmax; c++) {
+            const int warps = occ_for(c) * c;
+            if (warps >= best) {
+                best = warps;
+                W = c;
+            }
+        }
+    }
+    W = std::max(1, std::min(wmax, W));
+    h->warps = W;
+    h->smem = smem_for(W);
+    if ((int)h->smem > max_optin) return h->fail(RMDEC_EINVAL, "configuration needs %zu B shared memory (max %d)", h->smem, max_optin);
+    const int occ = occ_for(W);
     if (occ < 1) return h->fail(RMDEC_EINVAL, "kernel cannot be resident (smem %zu)", h->smem);
     h->blocks_per_sm = h->req_ctas ? std::min(h->req_ctas, occ) : occ;
     h->shape_dirty = false;
@@ -584,7 +600,7 @@ rmdec_status rmdec_autotune(rmdec_t h, int64_t n_frames, const char* cache_path,
     float best_ms = 1e30f;
     int best_w = 0;
     const int wmax = h->algo == 0 ? std::min(4, h->P) : 4;
-    for (int w = 1; w <= wmax; w *= 2) {
+    for (int w = 1; w <= wmax; w++) {
         h->req_warps = w;
         h->req_ctas = 0;
         h->shape_dirty = true;
