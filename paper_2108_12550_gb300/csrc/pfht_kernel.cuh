@@ -348,47 +348,30 @@ struct Decoder {
                 my_k = cidx & ((1 << S) - 1);
                 my_neg = (int)(imin & 1u);
             }
-            const int wk = cidx & ((1 << S) - 1);
-            const int owner = (cidx >> S) * G + (wk % G);
-            if (w.lane == owner) {
-                taken |= Mask(1) << (wk / G);
+            // the owner recognises itself: its key and index are the minimum
+            if (key == kmin && cid == imin) {
+                taken |= Mask(1) << ce;
                 used++;
-            }
-            if constexpr (E > DEPTH) {
-                if (q + 1 < L && __any_sync(kFull, used == DEPTH)) {
-                    // rare: a lane gave away both cached candidates. The node's input buffer
-                    // is free now; park the spectrum there and rescan it with a rolled loop.
-                    float* vb = const_cast<float*>(buf) + l * ST + g;
-                    if (act) {
-#pragma unroll
-                        for (int e = 0; e < E; e++) vb[G * e] = v[e];
-                    }
-                    __syncwarp();
-                    if (act && used == DEPTH) {
+                if constexpr (E > DEPTH) {
+                    if (used == DEPTH && q + 1 < L) {
+                        // rare: both cached candidates were taken; rescan the untaken ones
                         bool h1 = false, h2 = false;
-#pragma unroll 1
+#pragma unroll
                         for (int e = 0; e < E; e++) {
-                            if ((taken >> e) & 1) continue;
-                            const float a = vb[G * e];
-                            const bool g1 = !h1 || fabsf(a) > fabsf(c1);
-                            const bool g2 = !g1 && (!h2 || fabsf(a) > fabsf(c2));
-                            if (g1) {
-                                c2 = c1;
-                                e2 = e1;
-                                h2 = h1;
-                                c1 = a;
-                                e1 = e;
-                                h1 = true;
-                            } else if (g2) {
-                                c2 = a;
-                                e2 = e;
-                                h2 = true;
-                            }
+                            const float a = v[e];
+                            const bool ok = !((taken >> e) & 1);
+                            const bool g1 = ok && (!h1 || fabsf(a) > fabsf(c1));
+                            const bool g2 = ok && !g1 && (!h2 || fabsf(a) > fabsf(c2));
+                            c2 = g1 ? c1 : (g2 ? a : c2);
+                            e2 = g1 ? e1 : (g2 ? e : e2);
+                            h2 = h2 || g2 || (g1 && h1);
+                            c1 = g1 ? a : c1;
+                            e1 = g1 ? e : e1;
+                            h1 = h1 || g1;
                         }
                         avail = (h1 ? 1 : 0) + (h2 ? 1 : 0);
                         used = 0;
                     }
-                    __syncwarp();
                 }
             }
         }
@@ -811,7 +794,7 @@ struct Decoder {
 };
 
 template <int M, int R, int L>
-__global__ void __launch_bounds__(128, 4) pfht_kernel(LaunchArgs args) {
+__global__ void __launch_bounds__(128, 5) pfht_kernel(LaunchArgs args) {
     using C = Cfg<M, R, L>;
     using D = Decoder<M, R, L>;
     constexpr int N = C::N;
