@@ -23,6 +23,12 @@ PERM_REC = 11
 _lib = None
 
 
+class _Segment(ctypes.Structure):
+    """rmdec_segment (include/rmdec_group.h)."""
+    _fields_ = [("decoder", ctypes.c_int), ("llr_dev", ctypes.c_void_p), ("n_frames", ctypes.c_int64),
+                ("bits_out_dev", ctypes.c_void_p)]
+
+
 class RmdecError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"rmdec status {status}: {msg}")
@@ -61,6 +67,11 @@ def load_library():
         "rmdec_graph_create": ([V, V, I64, V, ctypes.POINTER(V)], I),
         "rmdec_graph_launch": ([V, V], I),
         "rmdec_graph_destroy": ([V], None),
+        "rmdec_group_create": ([ctypes.POINTER(V), ctypes.POINTER(V), I], I),
+        "rmdec_group_decode": ([V, ctypes.POINTER(_Segment), I, V], I),
+        "rmdec_group_set_tuning": ([V, I, I], I),
+        "rmdec_group_destroy": ([V], None),
+        "rmdec_group_last_error": ([V], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -236,6 +247,54 @@ class Graph:
             pass
 
 
+class Group:
+    """rmdec_group_t: one kernel launch over frames of several decoders (include/rmdec_group.h).
+    The decoders must be p-FHT-FSCL or FHT-FSCL handles with one list size L in {1, 2, 4}."""
+
+    def __init__(self, decoders):
+        lib = load_library()
+        self._lib = lib
+        arr = (ctypes.c_void_p * len(decoders))(*[d._h.value for d in decoders])
+        h = ctypes.c_void_p()
+        st = lib.rmdec_group_create(ctypes.byref(h), arr, len(decoders))
+        if st != OK:
+            raise RmdecError(st, lib.rmdec_group_last_error(None).decode())
+        self._h = h
+        self._decoders = list(decoders)  # the handles must outlive the group
+
+    def _check(self, st):
+        if st != OK:
+            raise RmdecError(st, self._lib.rmdec_group_last_error(self._h).decode())
+        return st
+
+    def decode(self, segments, stream=None):
+        """segments: list of (decoder index, llr CUDA tensor [F, n] of that decoder's dtype,
+        out CUDA int32 tensor [F, ceil(k/32)] or None). Returns the output tensors."""
+        arr = (_Segment * max(1, len(segments)))()
+        outs = []
+        for i, (d, llr, out) in enumerate(segments):
+            if out is None:
+                out = self._decoders[d]._alloc_bits(llr.shape[0], None)
+            arr[i] = _Segment(d, _ptr(llr), llr.shape[0], _ptr(out))
+            outs.append(out)
+        self._check(self._lib.rmdec_group_decode(self._h, arr, len(segments), _stream_ptr(stream)))
+        return outs
+
+    def set_tuning(self, warps_per_cta=0, ctas_per_sm=0):
+        self._check(self._lib.rmdec_group_set_tuning(self._h, warps_per_cta, ctas_per_sm))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.rmdec_group_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def unpack_bits(words, nbits):
     """[F, W] int32/uint32 words -> [F, nbits] uint8 (bit j = bit j%32 of word j//32)."""
     w = np.asarray(words).astype(np.uint32)
@@ -256,7 +315,7 @@ def pack_bits(bits):
 class _ServerConfig(ctypes.Structure):
     _fields_ = [("n_streams", ctypes.c_int), ("arena_bytes", ctypes.c_int64),
                 ("max_batch_frames", ctypes.c_int64), ("min_batch_frames", ctypes.c_int64),
-                ("max_wait_us", ctypes.c_int64)]
+                ("max_wait_us", ctypes.c_int64), ("fuse_codes", ctypes.c_int)]
 
 
 class _ServerStats(ctypes.Structure):
@@ -292,9 +351,10 @@ class Server:
     """Continuous-batching request server (include/rmdec_serve.h) over Decoder handles."""
 
     def __init__(self, n_streams=4, arena_bytes=1 << 30, max_batch_frames=1 << 16, min_batch_frames=0,
-                 max_wait_us=0):
+                 max_wait_us=0, fuse_codes=False):
         self._lib = _load_server_api(load_library())
-        cfg = _ServerConfig(n_streams, arena_bytes, max_batch_frames, min_batch_frames, max_wait_us)
+        cfg = _ServerConfig(n_streams, arena_bytes, max_batch_frames, min_batch_frames, max_wait_us,
+                            1 if fuse_codes else 0)
         h = ctypes.c_void_p()
         st = self._lib.rmdec_server_create(ctypes.byref(h), ctypes.byref(cfg))
         if st != OK:

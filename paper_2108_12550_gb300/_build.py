@@ -16,8 +16,10 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
                      "--expt-relaxed-constexpr"]
 
-UNITS = ["rmdec_api.cu", "autssc.cu", "serve.cu"] + [f"inst_m{m}.cu" for m in range(4, 10)]
-HEADERS = ["pfht_kernel.cuh", "rmdec_internal.h"]
+# slowest units first, so that they start first in the parallel build
+UNITS = (["group_l4.cu", "group_l2.cu", "group_l1.cu"] + [f"inst_m{m}.cu" for m in range(9, 3, -1)]
+         + ["rmdec_api.cu", "autssc.cu", "serve.cu", "group.cu"])
+HEADERS = ["pfht_kernel.cuh", "group_kernel.cuh", "rmdec_internal.h"]
 
 
 def _nvcc() -> str:
@@ -38,7 +40,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", h)
-                                                        for h in ("rmdec.h", "rmdec_serve.h")]
+                                                        for h in ("rmdec.h", "rmdec_serve.h", "rmdec_group.h")]
     objs, todo = [], []
     for u in UNITS:
         src = os.path.join(CSRC, u)

@@ -1,0 +1,228 @@
+// Host side of grouped multi-code decoding (see include/rmdec_group.h and group_kernel.cuh).
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/rmdec.h"
+#include "../../include/rmdec_group.h"
+#include "group_kernel.cuh"
+#include "rmdec_internal.h"
+
+namespace {
+thread_local std::string g_group_create_error;
+
+const void* group_fn(int L) {
+    switch (L) {
+        case 1: return rmdec_host::group_kernel_l1();
+        case 2: return rmdec_host::group_kernel_l2();
+        case 4: return rmdec_host::group_kernel_l4();
+    }
+    return nullptr;
+}
+}  // namespace
+
+struct rmdec_group {
+    std::vector<rmdec_t> decs;
+    int L = 0;
+    const void* fn = nullptr;
+    int device = -1;  // device the kernel attributes were set for
+    int sm_count = 0, max_optin = 0;
+    int req_warps = 0, req_ctas = 0;
+    std::string err;
+
+    rmdec_status fail(rmdec_status st, const char* fmt, ...) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        err = buf;
+        return st;
+    }
+};
+
+extern "C" {
+
+rmdec_status rmdec_group_create(rmdec_group_t* out, const rmdec_t* decoders, int n_decoders) {
+    if (!out) {
+        g_group_create_error = "null output pointer";
+        return RMDEC_EINVAL;
+    }
+    *out = nullptr;
+    if (!decoders || n_decoders < 1 || n_decoders > rmdec_dev::kGroupMaxDec) {
+        g_group_create_error = "need 1..16 decoder handles";
+        return RMDEC_EINVAL;
+    }
+    int L = 0;
+    for (int i = 0; i < n_decoders; i++) {
+        rmdec_host::MemberInfo mi;
+        if (!decoders[i] || rmdec_host::member_info(decoders[i], false, &mi) != RMDEC_OK) {
+            g_group_create_error = "null decoder handle at index " + std::to_string(i);
+            return RMDEC_EINVAL;
+        }
+        if (mi.algo != 0) {
+            g_group_create_error = "decoder " + std::to_string(i) + " is not a p-FHT-FSCL decoder";
+            return RMDEC_EINVAL;
+        }
+        if (!group_fn(mi.L)) {
+            g_group_create_error = "decoder " + std::to_string(i) + ": list size " + std::to_string(mi.L) +
+                                   " is not supported in groups (L in {1, 2, 4})";
+            return RMDEC_EINVAL;
+        }
+        if (i == 0) L = mi.L;
+        if (mi.L != L) {
+            g_group_create_error = "decoders of one group need the same list size";
+            return RMDEC_EINVAL;
+        }
+    }
+    rmdec_group* g = new (std::nothrow) rmdec_group;
+    if (!g) {
+        g_group_create_error = "host allocation failed";
+        return RMDEC_ENOMEM;
+    }
+    g->decs.assign(decoders, decoders + n_decoders);
+    g->L = L;
+    g->fn = group_fn(L);
+    *out = g;
+    return RMDEC_OK;
+}
+
+rmdec_status rmdec_group_decode(rmdec_group_t g, const rmdec_segment* segs, int n_segs, void* stream) {
+    using namespace rmdec_dev;
+    if (!g) return RMDEC_EINVAL;
+    if (n_segs < 0 || (n_segs > 0 && !segs)) return g->fail(RMDEC_EINVAL, "bad segment list");
+    const int nd = (int)g->decs.size();
+    for (int i = 0; i < n_segs; i++) {
+        const rmdec_segment& s = segs[i];
+        if (s.decoder < 0 || s.decoder >= nd) return g->fail(RMDEC_EINVAL, "segment %d: unknown decoder %d", i, s.decoder);
+        if (s.n_frames < 0) return g->fail(RMDEC_EINVAL, "segment %d: n_frames < 0", i);
+        if (s.n_frames == 0) continue;
+        if (!s.llr_dev || !s.bits_out_dev) return g->fail(RMDEC_EINVAL, "segment %d: null buffer", i);
+        if (reinterpret_cast<uintptr_t>(s.llr_dev) % 16) return g->fail(RMDEC_EINVAL, "segment %d: llr buffer must be 16-byte aligned", i);
+    }
+    // the members' current tables on this device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return g->fail(RMDEC_EDEVICE, "no CUDA device: %s", cudaGetErrorString(e));
+    std::vector<rmdec_host::MemberInfo> mi(nd);
+    std::vector<char> used(nd, 0);
+    for (int i = 0; i < n_segs; i++)
+        if (segs[i].n_frames > 0) used[segs[i].decoder] = 1;
+    int rec_cap = 0, k_cap = 0, n_cap = 0, stride = 0;
+    for (int d = 0; d < nd; d++) {
+        if (!used[d]) continue;
+        const rmdec_status st = rmdec_host::member_info(g->decs[d], true, &mi[d]);
+        if (st != RMDEC_OK) return g->fail(st, "decoder %d: %s", d, rmdec_last_error(g->decs[d]));
+        if (mi[d].device != dev) return g->fail(RMDEC_EINVAL, "decoder %d was prepared on device %d, current is %d", d, mi[d].device, dev);
+        if (mi[d].L != g->L || mi[d].algo != 0) return g->fail(RMDEC_EINVAL, "decoder %d no longer fits the group", d);
+        rec_cap = std::max(rec_cap, mi[d].P * mi[d].nrec * kRec);
+        k_cap = std::max(k_cap, mi[d].k);
+        n_cap = std::max(n_cap, mi[d].n);
+        stride = std::max(stride, mi[d].warp_bytes);
+    }
+    // non-empty segments, most work per frame first (stable, so equal costs keep caller order)
+    std::vector<int> order;
+    for (int i = 0; i < n_segs; i++)
+        if (segs[i].n_frames > 0) order.push_back(i);
+    if (order.empty()) return RMDEC_OK;
+    auto cost = [&](int i) {
+        const auto& m = mi[segs[i].decoder];
+        return (double)m.P * m.L * m.n * (m.m + m.r);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+
+    if (g->device != dev) {
+        if ((e = cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&g->max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+            return g->fail(RMDEC_ECUDA, "device attributes: %s", cudaGetErrorString(e));
+        if ((e = cudaFuncSetAttribute(g->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, g->max_optin)) != cudaSuccess)
+            return g->fail(RMDEC_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+        g->device = dev;
+    }
+    auto smem_for = [&](int W) { return (size_t)frame_fixed_bytes(rec_cap, k_cap, n_cap, W) + 16 + (size_t)W * stride; };
+    auto occ_for = [&](int W) {
+        int o = 0;
+        if (smem_for(W) > (size_t)g->max_optin) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, g->fn, 32 * W, smem_for(W)) != cudaSuccess) return 0;
+        return o;
+    };
+    int W = g->req_warps;
+    if (!W) {
+        int best = -1;
+        for (int c = 1; c <= 4; c++) {
+            const int warps = occ_for(c) * c;
+            if (warps >= best) {
+                best = warps;
+                W = c;
+            }
+        }
+    }
+    const int occ = occ_for(W);
+    if (occ < 1) return g->fail(RMDEC_EINVAL, "group launch cannot be resident (%zu B shared memory)", smem_for(W));
+    const int per_sm = g->req_ctas ? std::min(g->req_ctas, occ) : occ;
+
+    static_assert(sizeof(GroupArgs) <= 32000, "kernel parameter space");
+    GroupArgs a;
+    memset(&a, 0, sizeof a);
+    for (int d = 0; d < nd; d++) {
+        if (!used[d]) continue;
+        GroupDec& gd = a.dec[d];
+        gd.recs = mi[d].d_recs;
+        gd.info = mi[d].d_info;
+        gd.cfg = group_cfg_index(mi[d].m, mi[d].r);
+        gd.P = mi[d].P;
+        gd.K = mi[d].k;
+        gd.rec_elems = mi[d].P * mi[d].nrec * kRec;
+        gd.dtype = mi[d].dtype;
+        gd.qclamp = (float)((1 << (24 - mi[d].m)) - 1);
+        gd.single = mi[d].single;
+    }
+    a.rec_cap = rec_cap;
+    a.k_cap = k_cap;
+    a.warp_stride = stride;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (size_t lo = 0; lo < order.size(); lo += kGroupMaxSeg) {
+        const size_t hi = std::min(order.size(), lo + (size_t)kGroupMaxSeg);
+        int64_t total = 0;
+        for (size_t q = lo; q < hi; q++) {
+            const rmdec_segment& s = segs[order[q]];
+            GroupSeg& gs = a.seg[q - lo];
+            gs.llr = s.llr_dev;
+            gs.info_out = s.bits_out_dev;
+            gs.first = total;
+            gs.dec = s.decoder;
+            total += s.n_frames;
+        }
+        a.n_seg = (int)(hi - lo);
+        a.total = total;
+        const unsigned grid = (unsigned)std::min<int64_t>(total, (int64_t)g->sm_count * per_sm);
+        void* args[] = {&a};
+        if ((e = cudaLaunchKernel(g->fn, dim3(grid), dim3(32 * W), args, smem_for(W), st)) != cudaSuccess)
+            return g->fail(RMDEC_ECUDA, "group kernel launch: %s", cudaGetErrorString(e));
+    }
+    return RMDEC_OK;
+}
+
+rmdec_status rmdec_group_set_tuning(rmdec_group_t g, int warps_per_cta, int ctas_per_sm) {
+    if (!g) return RMDEC_EINVAL;
+    if (warps_per_cta < 0 || warps_per_cta > 4 || ctas_per_sm < 0)
+        return g->fail(RMDEC_EINVAL, "warps_per_cta must be 0..4 and ctas_per_sm >= 0");
+    g->req_warps = warps_per_cta;
+    g->req_ctas = ctas_per_sm;
+    return RMDEC_OK;
+}
+
+void rmdec_group_destroy(rmdec_group_t g) { delete g; }
+
+const char* rmdec_group_last_error(rmdec_group_t g) {
+    if (!g) return g_group_create_error.c_str();
+    return g->err.c_str();
+}
+
+}  // extern "C"

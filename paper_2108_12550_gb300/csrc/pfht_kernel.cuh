@@ -84,10 +84,7 @@ struct Cfg {
     static constexpr int OFF_BEST = OFF_XTMP + NW * 4;
     static constexpr int OFF_SPC = OFF_BEST + NW * 4;
     static constexpr int WARP_BYTES = ((OFF_SPC + L * 32) + 15) / 16 * 16;
-    static __host__ constexpr int fixed_bytes(int P, int K, int W) {
-        // records, info positions, frame LLRs, per-warp (pm, p) reduction slots
-        return ((P * NREC * kRec * 2 + K * 2 + 15) / 16) * 16 + N * 4 + W * 8;
-    }
+    static __host__ constexpr int fixed_bytes(int P, int K, int W);
 };
 
 struct Warp {
@@ -793,26 +790,65 @@ struct Decoder {
     }
 };
 
+// Block shared memory, common to every configuration: the decoders' permutation records,
+// the K information positions, the frame LLRs, per-warp (metric, decoder) reduction slots,
+// then one area of warp_stride bytes per warp.
+__host__ __device__ constexpr int frame_fixed_bytes(int rec_elems, int K, int N, int W) {
+    return ((rec_elems * 2 + K * 2 + 15) / 16) * 16 + N * 4 + W * 8;
+}
+
 template <int M, int R, int L>
-__global__ void __launch_bounds__(128, 5) pfht_kernel(LaunchArgs args) {
+__host__ constexpr int Cfg<M, R, L>::fixed_bytes(int P, int K, int W) {
+    return frame_fixed_bytes(P * NREC * kRec, K, N, W);
+}
+
+struct FrameSmem {
+    uint16_t* rec;    // records of the decoder being run
+    uint16_t* info;   // its information positions
+    float* y;         // frame LLRs; the reduction slots and warp areas follow the N of the code
+    int warp_stride;  // bytes per warp area
+};
+
+__device__ __forceinline__ FrameSmem carve_smem(uint8_t* smem, int rec_elems, int K, int warp_stride) {
+    FrameSmem s;
+    s.rec = reinterpret_cast<uint16_t*>(smem);
+    s.info = s.rec + rec_elems;
+    s.y = reinterpret_cast<float*>(smem + ((rec_elems * 2 + K * 2 + 15) / 16) * 16);
+    s.warp_stride = warp_stride;
+    return s;
+}
+
+// What the decode of one frame reads and writes (output pointers may be null except info_out).
+struct FrameJob {
+    const void* llr;     // [frames][N] of dtype
+    int dtype;
+    float qclamp;        // |code| clamp for I16 inputs
+    int P, K;
+    int single;          // one live initial path (FHT-FSCL without permutations)
+    uint32_t* info_out;  // [frames][ceil(K/32)]
+    uint32_t* cw_out;    // [frames][ceil(N/32)]
+    float* pm_out;       // [frames]
+    int32_t* best_out;   // [frames]
+};
+
+// Decodes frame f of a job with the whole block (Algorithm 5 over the P decoders, split
+// round-robin over the warps). The block's records and information positions must already
+// be in shared memory; the first barrier also publishes them.
+template <int M, int R, int L>
+__device__ __forceinline__ void decode_frame(const FrameJob& j, const FrameSmem& sm, int64_t f) {
     using C = Cfg<M, R, L>;
     using D = Decoder<M, R, L>;
     constexpr int N = C::N;
     constexpr int NW = C::NW;
-    extern __shared__ __align__(16) uint8_t smem[];
     const int W = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int P = args.P;
-    const int K = args.K;
-    uint16_t* s_rec = reinterpret_cast<uint16_t*>(smem);
-    uint16_t* s_info = s_rec + P * C::NREC * kRec;
-    float* s_y = reinterpret_cast<float*>(smem + ((P * C::NREC * kRec * 2 + K * 2 + 15) / 16) * 16);
+    float* s_y = sm.y;
     float* s_redpm = s_y + N;
     int* s_redp = reinterpret_cast<int*>(s_redpm + W);
     uint8_t* wbase = reinterpret_cast<uint8_t*>(s_redp + W);
     wbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(wbase) + 15) & ~uintptr_t(15));
-    uint8_t* mine = wbase + warp * C::WARP_BYTES;
+    uint8_t* mine = wbase + warp * sm.warp_stride;
     Warp w;
     w.alpha = reinterpret_cast<float*>(mine);
     w.bits = reinterpret_cast<uint32_t*>(mine + C::OFF_BITS);
@@ -821,99 +857,116 @@ __global__ void __launch_bounds__(128, 5) pfht_kernel(LaunchArgs args) {
     w.spc = mine + C::OFF_SPC;
     w.y = s_y;
     w.lane = lane;
-    w.single = args.single_start != 0;
+    w.single = j.single != 0;
 
-    for (int i = threadIdx.x; i < P * C::NREC * kRec; i += blockDim.x) s_rec[i] = args.recs[i];
-    for (int i = threadIdx.x; i < K; i += blockDim.x) s_info[i] = args.info[i];
-
-    for (int64_t f = blockIdx.x; f < args.n_frames; f += gridDim.x) {
-        __syncthreads();
-        // frame LLRs into shared memory, widened to float
-        if (args.dtype == IN_F32) {
-            const float4* src = reinterpret_cast<const float4*>(static_cast<const float*>(args.llr) + f * N);
-            for (int i = threadIdx.x; i < N / 4; i += blockDim.x) reinterpret_cast<float4*>(s_y)[i] = src[i];
-        } else if (args.dtype == IN_I8) {
-            const int8_t* src = static_cast<const int8_t*>(args.llr) + f * N;
-            for (int i = threadIdx.x; i < N; i += blockDim.x) s_y[i] = (float)src[i];
-        } else if (args.dtype == IN_F16) {
-            const __half* src = static_cast<const __half*>(args.llr) + f * N;
-            for (int i = threadIdx.x; i < N; i += blockDim.x) s_y[i] = __half2float(src[i]);
-        } else {
-            const int16_t* src = static_cast<const int16_t*>(args.llr) + f * N;
-            for (int i = threadIdx.x; i < N; i += blockDim.x)
-                s_y[i] = fminf(fmaxf((float)src[i], -args.qclamp), args.qclamp);
+    __syncthreads();
+    // frame LLRs into shared memory, widened to float
+    if (j.dtype == IN_F32) {
+        const float4* src = reinterpret_cast<const float4*>(static_cast<const float*>(j.llr) + f * N);
+        for (int i = threadIdx.x; i < N / 4; i += blockDim.x) reinterpret_cast<float4*>(s_y)[i] = src[i];
+    } else if (j.dtype == IN_I8) {
+        const int8_t* src = static_cast<const int8_t*>(j.llr) + f * N;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) s_y[i] = (float)src[i];
+    } else if (j.dtype == IN_F16) {
+        const __half* src = static_cast<const __half*>(j.llr) + f * N;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) s_y[i] = __half2float(src[i]);
+    } else {
+        const int16_t* src = static_cast<const int16_t*>(j.llr) + f * N;
+        for (int i = threadIdx.x; i < N; i += blockDim.x)
+            s_y[i] = fminf(fmaxf((float)src[i], -j.qclamp), j.qclamp);
+    }
+    __syncthreads();
+    float best = __int_as_float(0x7f800000);
+    int bestp = -1;
+    for (int p = warp; p < j.P; p += W) {
+        w.rec = sm.rec + p * C::NREC * kRec;
+        int c0;
+        const float pm = D::run(w, c0);
+        if (bestp < 0 || pm < best) {  // strict: earlier decoders win ties (Algorithm 5)
+            best = pm;
+            bestp = p;
+            D::emit(w, c0, w.best);
         }
-        __syncthreads();
-        float best = __int_as_float(0x7f800000);
-        int bestp = -1;
-        for (int p = warp; p < P; p += W) {
-            w.rec = s_rec + p * C::NREC * kRec;
-            int c0;
-            const float pm = D::run(w, c0);
-            if (bestp < 0 || pm < best) {  // strict: earlier decoders win ties (Algorithm 5)
-                best = pm;
-                bestp = p;
-                D::emit(w, c0, w.best);
+        __syncwarp();
+    }
+    if (lane == 0) {
+        s_redpm[warp] = best;
+        s_redp[warp] = bestp;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        // the winner over warps by (metric, decoder index)
+        float bp = __int_as_float(0x7f800000);
+        int bw = 0, bpp = 1 << 30;
+        for (int q = 0; q < W; q++) {
+            const float v = s_redpm[q];
+            const int pq = s_redp[q];
+            if (pq >= 0 && (v < bp || (v == bp && pq < bpp))) {
+                bp = v;
+                bpp = pq;
+                bw = q;
             }
-            __syncwarp();
         }
+        uint32_t* cw = reinterpret_cast<uint32_t*>(wbase + bw * sm.warp_stride + C::OFF_BEST);
+        if (j.cw_out)
+            for (int wd = lane; wd < NW; wd += 32) j.cw_out[f * NW + wd] = cw[wd];
         if (lane == 0) {
-            s_redpm[warp] = best;
-            s_redp[warp] = bestp;
+            if (j.pm_out) j.pm_out[f] = bp;
+            if (j.best_out) j.best_out[f] = bpp;
         }
-        __syncthreads();
-        if (warp == 0) {
-            // the winner over warps by (metric, decoder index)
-            float bp = __int_as_float(0x7f800000);
-            int bw = 0, bpp = 1 << 30;
-            for (int q = 0; q < W; q++) {
-                const float v = s_redpm[q];
-                const int pq = s_redp[q];
-                if (pq >= 0 && (v < bp || (v == bp && pq < bpp))) {
-                    bp = v;
-                    bpp = pq;
-                    bw = q;
-                }
-            }
-            uint32_t* cw = reinterpret_cast<uint32_t*>(wbase + bw * C::WARP_BYTES + C::OFF_BEST);
-            if (args.cw_out)
-                for (int wd = lane; wd < NW; wd += 32) args.cw_out[f * NW + wd] = cw[wd];
-            if (lane == 0) {
-                if (args.pm_out) args.pm_out[f] = bp;
-                if (args.best_out) args.best_out[f] = bpp;
-            }
-            // u = x G^{(x)m}: u_i = XOR of x_j over j containing i
-            uint32_t* u = w.xtmp;
-            for (int wd = lane; wd < NW; wd += 32) {
-                unsigned v = cw[wd];
-                if (M > 0) v ^= (v >> 1) & 0x55555555u;
-                if (M > 1) v ^= (v >> 2) & 0x33333333u;
-                if (M > 2) v ^= (v >> 4) & 0x0F0F0F0Fu;
-                if (M > 3) v ^= (v >> 8) & 0x00FF00FFu;
-                if (M > 4) v ^= (v >> 16) & 0x0000FFFFu;
-                u[wd] = v;
-            }
-            __syncwarp();
+        // u = x G^{(x)m}: u_i = XOR of x_j over j containing i
+        uint32_t* u = w.xtmp;
+        for (int wd = lane; wd < NW; wd += 32) {
+            unsigned v = cw[wd];
+            if (M > 0) v ^= (v >> 1) & 0x55555555u;
+            if (M > 1) v ^= (v >> 2) & 0x33333333u;
+            if (M > 2) v ^= (v >> 4) & 0x0F0F0F0Fu;
+            if (M > 3) v ^= (v >> 8) & 0x00FF00FFu;
+            if (M > 4) v ^= (v >> 16) & 0x0000FFFFu;
+            u[wd] = v;
+        }
+        __syncwarp();
 #pragma unroll
-            for (int t = 5; t < M; t++) {
-                const int d = 1 << (t - 5);
-                for (int wd = lane; wd < NW; wd += 32)
-                    if (!(wd & d)) u[wd] ^= u[wd | d];
-                __syncwarp();
+        for (int t = 5; t < M; t++) {
+            const int d = 1 << (t - 5);
+            for (int wd = lane; wd < NW; wd += 32)
+                if (!(wd & d)) u[wd] ^= u[wd | d];
+            __syncwarp();
+        }
+        const int KW = (j.K + 31) / 32;
+        for (int it = 0; it < KW; it++) {
+            const int jj = lane + 32 * it;
+            unsigned bit = 0;
+            if (jj < j.K) {
+                const int pos = sm.info[jj];
+                bit = (u[pos >> 5] >> (pos & 31)) & 1u;
             }
-            const int KW = (K + 31) / 32;
-            for (int it = 0; it < KW; it++) {
-                const int j = lane + 32 * it;
-                unsigned bit = 0;
-                if (j < K) {
-                    const int pos = s_info[j];
-                    bit = (u[pos >> 5] >> (pos & 31)) & 1u;
-                }
-                const unsigned word = __ballot_sync(kFull, bit);
-                if (lane == 0) args.info_out[f * KW + it] = word;
-            }
+            const unsigned word = __ballot_sync(kFull, bit);
+            if (lane == 0) j.info_out[f * KW + it] = word;
         }
     }
+}
+
+template <int M, int R, int L>
+__global__ void __launch_bounds__(128, 5) pfht_kernel(LaunchArgs args) {
+    using C = Cfg<M, R, L>;
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int rec_elems = args.P * C::NREC * kRec;
+    const FrameSmem sm = carve_smem(smem, rec_elems, args.K, C::WARP_BYTES);
+    for (int i = threadIdx.x; i < rec_elems; i += blockDim.x) sm.rec[i] = args.recs[i];
+    for (int i = threadIdx.x; i < args.K; i += blockDim.x) sm.info[i] = args.info[i];
+    FrameJob j;
+    j.llr = args.llr;
+    j.dtype = args.dtype;
+    j.qclamp = args.qclamp;
+    j.P = args.P;
+    j.K = args.K;
+    j.single = args.single_start;
+    j.info_out = args.info_out;
+    j.cw_out = args.cw_out;
+    j.pm_out = args.pm_out;
+    j.best_out = args.best_out;
+    for (int64_t f = blockIdx.x; f < args.n_frames; f += gridDim.x) decode_frame<M, R, L>(j, sm, f);
 }
 
 }  // namespace rmdec_dev

@@ -354,6 +354,29 @@ rmdec_status make_handle(rmdec_t* out, int algo, int m, int r, int P, int L, uin
 
 namespace rmdec_host {
 size_t llr_elem_bytes_of(rmdec_ctx* h) { return llr_elem_bytes(h->dtype); }
+
+rmdec_status member_info(rmdec_ctx* h, bool prepare, MemberInfo* out) {
+    if (!h || !out) return RMDEC_EINVAL;
+    if (prepare) {
+        const rmdec_status st = ensure_device(h);
+        if (st != RMDEC_OK) return st;
+    }
+    out->algo = h->algo;
+    out->m = h->m;
+    out->r = h->r;
+    out->L = h->L;
+    out->P = h->P;
+    out->n = h->n;
+    out->k = h->k;
+    out->single = h->single_start ? 1 : 0;
+    out->dtype = (int)h->dtype;
+    out->d_recs = h->dirty ? nullptr : h->d_recs;
+    out->d_info = h->dirty ? nullptr : h->d_info;
+    out->warp_bytes = h->dirty ? 0 : h->kern.warp_bytes;
+    out->nrec = h->dirty ? 0 : h->kern.nrec;
+    out->device = h->dirty ? -1 : h->device;
+    return RMDEC_OK;
+}
 }  // namespace rmdec_host
 
 extern "C" {

@@ -6,6 +6,8 @@
 
 #include <cuda_runtime.h>
 
+#include "../../include/rmdec.h"
+
 struct rmdec_ctx;
 
 namespace rmdec_host {
@@ -31,6 +33,27 @@ bool lookup_pfht_m9(int r, int L, KernelEntry* e);
 
 // Aut-SSC baseline kernels (autssc.cu).
 bool lookup_autssc(int m, int r, KernelEntry* e);
+
+// What a grouped launch needs to know about one decoder handle.
+struct MemberInfo {
+    int algo = 0;  // 0: p-FHT-FSCL (and FHT-FSCL), 1: Aut-SSC
+    int m = 0, r = 0, L = 0, P = 0, n = 0, k = 0;
+    int single = 0;
+    int dtype = 0;
+    const uint16_t* d_recs = nullptr;  // valid after prepare
+    const uint16_t* d_info = nullptr;
+    int warp_bytes = 0;
+    int nrec = 0;  // device records per decoder
+    int device = -1;
+};
+// Fills *out from the handle; with prepare = true first uploads the handle's tables to the
+// current device (errors are recorded on the handle, see rmdec_last_error).
+rmdec_status member_info(rmdec_ctx* h, bool prepare, MemberInfo* out);
+
+// Grouped multi-code kernels (group_l<L>.cu), one per supported list size.
+const void* group_kernel_l1();
+const void* group_kernel_l2();
+const void* group_kernel_l4();
 
 }  // namespace rmdec_host
 

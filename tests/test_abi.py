@@ -14,7 +14,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    txt = "".join(open(os.path.join(ROOT, "include", h)).read() for h in ("rmdec.h", "rmdec_serve.h"))
+    txt = "".join(open(os.path.join(ROOT, "include", h)).read() for h in ("rmdec.h", "rmdec_serve.h",
+                                                                          "rmdec_group.h"))
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     return sorted(set(re.findall(r"\b(rmdec_[a-z0-9_]+)\s*\(", txt)))
 
@@ -22,7 +23,7 @@ def _declared():
 def test_library_exports_every_declared_symbol():
     lib = pkg.load_library()
     names = _declared()
-    assert len(names) >= 27
+    assert len(names) >= 32
     for n in names:
         assert hasattr(lib, n), n
 
@@ -80,3 +81,33 @@ def test_pack_unpack_roundtrip():
     rng = np.random.default_rng(0)
     b = rng.integers(0, 2, (5, 46), dtype=np.uint8)
     assert np.array_equal(pkg.unpack_bits(pkg.pack_bits(b), 46), b)
+
+
+def test_group_membership_is_validated_on_the_host():
+    lib = pkg.load_library()
+    a = pkg.Decoder(7, 2, 8, 4)
+    b = pkg.Decoder(9, 3, 2, 4, dtype="i8")
+    c = pkg.Decoder(9, 2, 4, 2)
+    s = pkg.Decoder(9, 2, 8, algo="autssc")
+    e = pkg.Decoder(9, 2, 2, 8)
+    f = pkg.Decoder(8, 2, 1, 4, algo="fhtfscl")
+    ok = pkg.Group([a, b, f])  # host-side only: no device work at creation
+    for bad in ([a, c], [a, s], [e], []):
+        with pytest.raises(pkg.RmdecError) as ei:
+            pkg.Group(bad)
+        assert ei.value.status == pkg.EINVAL
+        assert lib.rmdec_group_last_error(None)
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * 17)(*([a._h.value] * 17))
+    assert lib.rmdec_group_create(ctypes.byref(h), arr, 17) == pkg.EINVAL
+    # bad segments are rejected before any device work
+    seg = (pkg._Segment * 2)(pkg._Segment(0, None, 0, None), pkg._Segment(3, None, 0, None))
+    assert lib.rmdec_group_decode(ok._h, seg, 2, None) == pkg.EINVAL
+    seg = (pkg._Segment * 1)(pkg._Segment(1, None, 5, None))
+    assert lib.rmdec_group_decode(ok._h, seg, 1, None) == pkg.EINVAL
+    seg = (pkg._Segment * 1)(pkg._Segment(1, 0x1008, 5, 0x2000))
+    assert lib.rmdec_group_decode(ok._h, seg, 1, None) == pkg.EINVAL  # misaligned LLRs
+    assert b"aligned" in lib.rmdec_group_last_error(ok._h)
+    assert lib.rmdec_group_decode(ok._h, None, 1, None) == pkg.EINVAL
+    assert lib.rmdec_group_set_tuning(ok._h, 5, 0) == pkg.EINVAL
+    ok.close()
