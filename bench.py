@@ -188,26 +188,34 @@ def run_serving(args):
         d.decode_host(pools[(ci, 0)], torch.zeros((pool_frames, d.kw), dtype=torch.int32))
     torch.cuda.synchronize()
 
-    # continuous-batching server
-    srv = pkg.Server(n_streams=args.streams, arena_bytes=2 << 30, max_batch_frames=1 << 15,
-                     min_batch_frames=1024, max_wait_us=500)
-    ids = [srv.add_decoder(d) for d in decs]
-    t0 = time.perf_counter()
-    rids = []
-    for ci, x, out, at in trace:
-        while time.perf_counter() - t0 < at:
-            pass
-        rids.append(srv.submit(ids[ci], x, out))
-    lat = []
-    for rid in rids:
-        st, l_us = srv.poll(rid, timeout_us=120_000_000)
-        if st != pkg.OK:
-            raise RuntimeError(f"serving request failed: {st}")
-        lat.append(l_us)
-    t_srv = time.perf_counter() - t0
-    stats = srv.stats()
-    srv.close()
-    served = [t[2].clone() for t in trace]
+    def serve(fuse):
+        """Replays the trace through the continuous-batching server; fuse = one grouped launch
+        per batch over all codes (else one launch per code)."""
+        for t in trace:
+            t[2].zero_()
+        srv = pkg.Server(n_streams=args.streams, arena_bytes=2 << 30, max_batch_frames=1 << 15,
+                         min_batch_frames=1024, max_wait_us=500, fuse_codes=fuse)
+        ids = [srv.add_decoder(d) for d in decs]
+        t0 = time.perf_counter()
+        rids = []
+        for ci, x, out, at in trace:
+            while time.perf_counter() - t0 < at:
+                pass
+            rids.append(srv.submit(ids[ci], x, out))
+        lat = []
+        for rid in rids:
+            st, l_us = srv.poll(rid, timeout_us=120_000_000)
+            if st != pkg.OK:
+                raise RuntimeError(f"serving request failed: {st}")
+            lat.append(l_us)
+        t_srv = time.perf_counter() - t0
+        stats = srv.stats()
+        srv.close()
+        return t_srv, lat, stats, [t[2].clone() for t in trace]
+
+    serve(True)  # warm-up: first grouped launches, host page-in of the trace
+    t_fused, lat_f, stats_f, served_f = serve(True)
+    t_srv, lat, stats, served = serve(False)
 
     # plain per-request launch: one synchronous host-to-host decode per request, in order
     s = torch.cuda.current_stream()
@@ -219,7 +227,7 @@ def run_serving(args):
         decs[ci].decode_host(x, out, s)
         plat.append((time.perf_counter() - t0 - at) * 1e6)
     t_plain = time.perf_counter() - t0
-    same = all(torch.equal(a, t[2]) for a, t in zip(served, trace))
+    same = all(torch.equal(a, t[2]) and torch.equal(b, t[2]) for a, b, t in zip(served, served_f, trace))
     line = {
         "metric": "frames/s serving mix (Poisson arrivals, mixed RM codes, P in {8,20}, L=4, INT8/FP32)",
         "value": total_frames / t_srv, "unit": "frames/s", "n_gpus": 1, "higher_is_better": True,
@@ -228,11 +236,16 @@ def run_serving(args):
                    "streams": args.streams, "codes": ["RM(2,7)", "RM(2,8)", "RM(2,9)", "RM(3,9)"]},
         "latency_us": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "max": float(np.max(lat))},
-        "server": {k: stats[k] for k in ("batches", "completed", "frames_completed")},
+        "server": {"fuse_codes": False, **{k: stats[k] for k in ("batches", "completed", "frames_completed")}},
+        "server_fused": {"value": total_frames / t_fused, "unit": "frames/s", "batches": stats_f["batches"],
+                         "latency_us": {"p50": float(np.percentile(lat_f, 50)),
+                                        "p99": float(np.percentile(lat_f, 99))},
+                         "form": "small requests of all 16 codes share grouped launches"},
         "plain_per_request": {"value": total_frames / t_plain, "unit": "frames/s",
                               "latency_us": {"p50": float(np.percentile(plat, 50)),
                                              "p99": float(np.percentile(plat, 99))}},
         "results_identical_alone_and_in_mix": bool(same),
+        "gpu_launches": int(stats["batches"]),  # one decode launch per batch
     }
     print(json.dumps(line), flush=True)
 

@@ -6,7 +6,10 @@
  * over the handle's P decoders, each following Algorithm 2 with FHTL nodes, Algorithms 3-4
  * and Eq. (8), and SPCL nodes, Eqs. (2)-(6), of arXiv 2108.12550): results are bit-identical.
  * Grouping is not part of the paper's method; it packs uneven work into one persistent
- * launch, so that many small per-code batches need neither a launch each nor a stream each.
+ * launch, so that many small per-code batches need neither a launch each nor a stream each
+ * and together fill the GPU. A grouped launch runs every member with the largest member's
+ * shared-memory and register footprint, so segments large enough to fill the GPU on their
+ * own are better off in their decoder's own launch, and by default go there.
  *
  * Members: p-FHT-FSCL and FHT-FSCL handles (rmdec_create, rmdec_create_fhtfscl) that share
  * one list size L in {1, 2, 4}; any (m, r) those constructors accept, any P, any dtype.
@@ -40,12 +43,19 @@ typedef struct {
 rmdec_status rmdec_group_create(rmdec_group_t *out, const rmdec_t *decoders, int n_decoders);
 
 /* Decodes n_segs segments, asynchronously on `stream` (a cudaStream_t, NULL = default
- * stream). Segments are ordered by decreasing work per frame and run in one launch (more
- * than 224 segments take several launches on the same stream). Uploads member tables on
- * first use (synchronous), so call once before any stream capture. RMDEC_EINVAL for a bad
- * segment (unknown decoder, negative count, null or misaligned pointer); nothing is
- * launched then. */
+ * stream). Segments too small to fill the GPU alone (see rmdec_group_set_split) are ordered
+ * by decreasing work per frame and share one grouped launch (more than 224 such segments
+ * take several launches); each larger segment then runs in its own decoder's launch, which
+ * keeps that decoder's own occupancy. All launches go to `stream` in that order. Uploads
+ * member tables on first use (synchronous), so call once before any stream capture.
+ * RMDEC_EINVAL for a bad segment (unknown decoder, negative count, null or misaligned
+ * pointer); nothing is launched then. */
 rmdec_status rmdec_group_decode(rmdec_group_t g, const rmdec_segment *segs, int n_segs, void *stream);
+
+/* Which segments leave the grouped launch: those of at least min_frames_alone frames
+ * (0, the default: one full wave of the decoder's own launch, i.e. SMs x its resident
+ * CTAs; < 0: none, every segment is grouped). Never changes results. */
+rmdec_status rmdec_group_set_split(rmdec_group_t g, int64_t min_frames_alone);
 
 /* Launch shape of the group's launches: warps per CTA (1..4, 0 = the most resident warps)
  * and a cap on CTAs per SM (0 = the occupancy limit). Never changes results. */

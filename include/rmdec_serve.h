@@ -5,8 +5,9 @@
  * serving layer for many concurrent decode requests of mixed codes: requests arrive on any
  * host thread, are admitted as device memory frees up, are packed per code into batches as
  * CUDA streams free up, and complete independently. Decoding itself is rmdec_decode
- * (include/rmdec.h); every frame is decoded independently, so a request's result does not
- * depend on what it was batched with.
+ * (include/rmdec.h), or rmdec_group_decode for batches that mix codes; every frame is decoded
+ * independently and identically either way, so a request's result does not depend on what it
+ * was batched with.
  *
  * Threading: all CUDA work runs on one worker thread owned by the server; submit/poll/stats
  * may be called from any thread. Decoder handles registered with a server must not be used
@@ -32,6 +33,11 @@ typedef struct {
     int64_t max_batch_frames; /* frames per batch cap (one kernel launch) */
     int64_t min_batch_frames; /* a batch waits up to max_wait_us for this many frames */
     int64_t max_wait_us;      /* longest time a request waits for batch companions */
+    int fuse_codes;           /* 1: batch small requests (below one full wave of their code's own
+                               * launch) of different codes that can share a grouped launch
+                               * (include/rmdec_group.h: p-FHT-FSCL decoders of one list size L in
+                               * {1, 2, 4}, up to 16 codes per family) and decode them with one
+                               * rmdec_group_decode call; 0: one code per batch */
 } rmdec_server_config;
 
 typedef struct {

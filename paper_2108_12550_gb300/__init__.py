@@ -70,6 +70,7 @@ def load_library():
         "rmdec_group_create": ([ctypes.POINTER(V), ctypes.POINTER(V), I], I),
         "rmdec_group_decode": ([V, ctypes.POINTER(_Segment), I, V], I),
         "rmdec_group_set_tuning": ([V, I, I], I),
+        "rmdec_group_set_split": ([V, I64], I),
         "rmdec_group_destroy": ([V], None),
         "rmdec_group_last_error": ([V], ctypes.c_char_p),
     }
@@ -282,6 +283,11 @@ class Group:
 
     def set_tuning(self, warps_per_cta=0, ctas_per_sm=0):
         self._check(self._lib.rmdec_group_set_tuning(self._h, warps_per_cta, ctas_per_sm))
+
+    def set_split(self, min_frames_alone=0):
+        """Segments of at least this many frames run in their own decoder's launch (0: one full
+        wave of that launch; negative: every segment stays in the grouped launch)."""
+        self._check(self._lib.rmdec_group_set_split(self._h, int(min_frames_alone)))
 
     def close(self):
         if getattr(self, "_h", None):

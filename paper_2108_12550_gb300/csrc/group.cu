@@ -34,6 +34,7 @@ struct rmdec_group {
     int device = -1;  // device the kernel attributes were set for
     int sm_count = 0, max_optin = 0;
     int req_warps = 0, req_ctas = 0;
+    int64_t min_alone = 0;  // 0: one full wave of the decoder's own launch; < 0: never alone
     std::string err;
 
     rmdec_status fail(rmdec_status st, const char* fmt, ...) {
@@ -46,6 +47,101 @@ struct rmdec_group {
         return st;
     }
 };
+
+namespace {
+// One or more group_kernel launches over the segments `order` (all non-empty).
+rmdec_status launch_grouped(rmdec_group* g, const rmdec_segment* segs, std::vector<int>& order,
+                            const std::vector<rmdec_host::MemberInfo>& mi, int dev, cudaStream_t st) {
+    using namespace rmdec_dev;
+    cudaError_t e;
+    const int nd = (int)g->decs.size();
+    std::vector<char> used(nd, 0);
+    for (int i : order) used[segs[i].decoder] = 1;
+    int rec_cap = 0, k_cap = 0, n_cap = 0, stride = 0;
+    for (int d = 0; d < nd; d++) {
+        if (!used[d]) continue;
+        rec_cap = std::max(rec_cap, mi[d].P * mi[d].nrec * kRec);
+        k_cap = std::max(k_cap, mi[d].k);
+        n_cap = std::max(n_cap, mi[d].n);
+        stride = std::max(stride, mi[d].warp_bytes);
+    }
+    auto cost = [&](int i) {
+        const auto& m = mi[segs[i].decoder];
+        return (double)m.P * m.L * m.n * (m.m + m.r);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+
+    if (g->device != dev) {
+        if ((e = cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&g->max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+            return g->fail(RMDEC_ECUDA, "device attributes: %s", cudaGetErrorString(e));
+        if ((e = cudaFuncSetAttribute(g->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, g->max_optin)) != cudaSuccess)
+            return g->fail(RMDEC_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+        g->device = dev;
+    }
+    auto smem_for = [&](int W) { return (size_t)frame_fixed_bytes(rec_cap, k_cap, n_cap, W) + 16 + (size_t)W * stride; };
+    auto occ_for = [&](int W) {
+        int o = 0;
+        if (smem_for(W) > (size_t)g->max_optin) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, g->fn, 32 * W, smem_for(W)) != cudaSuccess) return 0;
+        return o;
+    };
+    int W = g->req_warps;
+    if (!W) {
+        int best = -1;
+        for (int c = 1; c <= 4; c++) {
+            const int warps = occ_for(c) * c;
+            if (warps >= best) {
+                best = warps;
+                W = c;
+            }
+        }
+    }
+    const int occ = occ_for(W);
+    if (occ < 1) return g->fail(RMDEC_EINVAL, "group launch cannot be resident (%zu B shared memory)", smem_for(W));
+    const int per_sm = g->req_ctas ? std::min(g->req_ctas, occ) : occ;
+
+    static_assert(sizeof(GroupArgs) <= 32000, "kernel parameter space");
+    GroupArgs a;
+    memset(&a, 0, sizeof a);
+    for (int d = 0; d < nd; d++) {
+        if (!used[d]) continue;
+        GroupDec& gd = a.dec[d];
+        gd.recs = mi[d].d_recs;
+        gd.info = mi[d].d_info;
+        gd.cfg = group_cfg_index(mi[d].m, mi[d].r);
+        gd.P = mi[d].P;
+        gd.K = mi[d].k;
+        gd.rec_elems = mi[d].P * mi[d].nrec * kRec;
+        gd.dtype = mi[d].dtype;
+        gd.qclamp = (float)((1 << (24 - mi[d].m)) - 1);
+        gd.single = mi[d].single;
+    }
+    a.rec_cap = rec_cap;
+    a.k_cap = k_cap;
+    a.warp_stride = stride;
+    for (size_t lo = 0; lo < order.size(); lo += kGroupMaxSeg) {
+        const size_t hi = std::min(order.size(), lo + (size_t)kGroupMaxSeg);
+        int64_t total = 0;
+        for (size_t q = lo; q < hi; q++) {
+            const rmdec_segment& s = segs[order[q]];
+            GroupSeg& gs = a.seg[q - lo];
+            gs.llr = s.llr_dev;
+            gs.info_out = s.bits_out_dev;
+            gs.first = total;
+            gs.dec = s.decoder;
+            total += s.n_frames;
+        }
+        a.n_seg = (int)(hi - lo);
+        a.total = total;
+        const unsigned grid = (unsigned)std::min<int64_t>(total, (int64_t)g->sm_count * per_sm);
+        void* args[] = {&a};
+        if ((e = cudaLaunchKernel(g->fn, dim3(grid), dim3(32 * W), args, smem_for(W), st)) != cudaSuccess)
+            return g->fail(RMDEC_ECUDA, "group kernel launch: %s", cudaGetErrorString(e));
+    }
+    return RMDEC_OK;
+}
+}  // namespace
 
 extern "C" {
 
@@ -114,98 +210,40 @@ rmdec_status rmdec_group_decode(rmdec_group_t g, const rmdec_segment* segs, int 
     std::vector<char> used(nd, 0);
     for (int i = 0; i < n_segs; i++)
         if (segs[i].n_frames > 0) used[segs[i].decoder] = 1;
-    int rec_cap = 0, k_cap = 0, n_cap = 0, stride = 0;
     for (int d = 0; d < nd; d++) {
         if (!used[d]) continue;
         const rmdec_status st = rmdec_host::member_info(g->decs[d], true, &mi[d]);
         if (st != RMDEC_OK) return g->fail(st, "decoder %d: %s", d, rmdec_last_error(g->decs[d]));
         if (mi[d].device != dev) return g->fail(RMDEC_EINVAL, "decoder %d was prepared on device %d, current is %d", d, mi[d].device, dev);
         if (mi[d].L != g->L || mi[d].algo != 0) return g->fail(RMDEC_EINVAL, "decoder %d no longer fits the group", d);
-        rec_cap = std::max(rec_cap, mi[d].P * mi[d].nrec * kRec);
-        k_cap = std::max(k_cap, mi[d].k);
-        n_cap = std::max(n_cap, mi[d].n);
-        stride = std::max(stride, mi[d].warp_bytes);
     }
-    // non-empty segments, most work per frame first (stable, so equal costs keep caller order)
-    std::vector<int> order;
-    for (int i = 0; i < n_segs; i++)
-        if (segs[i].n_frames > 0) order.push_back(i);
-    if (order.empty()) return RMDEC_OK;
-    auto cost = [&](int i) {
-        const auto& m = mi[segs[i].decoder];
-        return (double)m.P * m.L * m.n * (m.m + m.r);
-    };
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
-
-    if (g->device != dev) {
-        if ((e = cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
-            (e = cudaDeviceGetAttribute(&g->max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
-            return g->fail(RMDEC_ECUDA, "device attributes: %s", cudaGetErrorString(e));
-        if ((e = cudaFuncSetAttribute(g->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, g->max_optin)) != cudaSuccess)
-            return g->fail(RMDEC_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-        g->device = dev;
+    // Segments that fill at least min_alone frames (default: one full wave of their decoder's
+    // own launch) run in their decoder's own kernel, which keeps its own register and
+    // shared-memory footprint; the rest share grouped launches, most work per frame first
+    // (stable, so equal costs keep the caller's order).
+    std::vector<int> order, alone;
+    for (int i = 0; i < n_segs; i++) {
+        if (segs[i].n_frames == 0) continue;
+        const int64_t thr = g->min_alone > 0 ? g->min_alone : mi[segs[i].decoder].wave;
+        if (g->min_alone >= 0 && segs[i].n_frames >= thr) alone.push_back(i);
+        else order.push_back(i);
     }
-    auto smem_for = [&](int W) { return (size_t)frame_fixed_bytes(rec_cap, k_cap, n_cap, W) + 16 + (size_t)W * stride; };
-    auto occ_for = [&](int W) {
-        int o = 0;
-        if (smem_for(W) > (size_t)g->max_optin) return 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, g->fn, 32 * W, smem_for(W)) != cudaSuccess) return 0;
-        return o;
-    };
-    int W = g->req_warps;
-    if (!W) {
-        int best = -1;
-        for (int c = 1; c <= 4; c++) {
-            const int warps = occ_for(c) * c;
-            if (warps >= best) {
-                best = warps;
-                W = c;
-            }
-        }
-    }
-    const int occ = occ_for(W);
-    if (occ < 1) return g->fail(RMDEC_EINVAL, "group launch cannot be resident (%zu B shared memory)", smem_for(W));
-    const int per_sm = g->req_ctas ? std::min(g->req_ctas, occ) : occ;
-
-    static_assert(sizeof(GroupArgs) <= 32000, "kernel parameter space");
-    GroupArgs a;
-    memset(&a, 0, sizeof a);
-    for (int d = 0; d < nd; d++) {
-        if (!used[d]) continue;
-        GroupDec& gd = a.dec[d];
-        gd.recs = mi[d].d_recs;
-        gd.info = mi[d].d_info;
-        gd.cfg = group_cfg_index(mi[d].m, mi[d].r);
-        gd.P = mi[d].P;
-        gd.K = mi[d].k;
-        gd.rec_elems = mi[d].P * mi[d].nrec * kRec;
-        gd.dtype = mi[d].dtype;
-        gd.qclamp = (float)((1 << (24 - mi[d].m)) - 1);
-        gd.single = mi[d].single;
-    }
-    a.rec_cap = rec_cap;
-    a.k_cap = k_cap;
-    a.warp_stride = stride;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    for (size_t lo = 0; lo < order.size(); lo += kGroupMaxSeg) {
-        const size_t hi = std::min(order.size(), lo + (size_t)kGroupMaxSeg);
-        int64_t total = 0;
-        for (size_t q = lo; q < hi; q++) {
-            const rmdec_segment& s = segs[order[q]];
-            GroupSeg& gs = a.seg[q - lo];
-            gs.llr = s.llr_dev;
-            gs.info_out = s.bits_out_dev;
-            gs.first = total;
-            gs.dec = s.decoder;
-            total += s.n_frames;
-        }
-        a.n_seg = (int)(hi - lo);
-        a.total = total;
-        const unsigned grid = (unsigned)std::min<int64_t>(total, (int64_t)g->sm_count * per_sm);
-        void* args[] = {&a};
-        if ((e = cudaLaunchKernel(g->fn, dim3(grid), dim3(32 * W), args, smem_for(W), st)) != cudaSuccess)
-            return g->fail(RMDEC_ECUDA, "group kernel launch: %s", cudaGetErrorString(e));
+    if (!order.empty()) {
+        const rmdec_status gs = launch_grouped(g, segs, order, mi, dev, st);
+        if (gs != RMDEC_OK) return gs;
     }
+    for (int i : alone) {
+        const rmdec_segment& s = segs[i];
+        const rmdec_status ds = rmdec_decode(g->decs[s.decoder], s.llr_dev, s.n_frames, s.bits_out_dev, st);
+        if (ds != RMDEC_OK) return g->fail(ds, "decoder %d: %s", s.decoder, rmdec_last_error(g->decs[s.decoder]));
+    }
+    return RMDEC_OK;
+}
+
+rmdec_status rmdec_group_set_split(rmdec_group_t g, int64_t min_frames_alone) {
+    if (!g) return RMDEC_EINVAL;
+    g->min_alone = min_frames_alone < 0 ? -1 : min_frames_alone;
     return RMDEC_OK;
 }
 

@@ -358,7 +358,8 @@ size_t llr_elem_bytes_of(rmdec_ctx* h) { return llr_elem_bytes(h->dtype); }
 rmdec_status member_info(rmdec_ctx* h, bool prepare, MemberInfo* out) {
     if (!h || !out) return RMDEC_EINVAL;
     if (prepare) {
-        const rmdec_status st = ensure_device(h);
+        rmdec_status st = ensure_device(h);
+        if (st == RMDEC_OK) st = configure_shape(h);
         if (st != RMDEC_OK) return st;
     }
     out->algo = h->algo;
@@ -375,6 +376,7 @@ rmdec_status member_info(rmdec_ctx* h, bool prepare, MemberInfo* out) {
     out->warp_bytes = h->dirty ? 0 : h->kern.warp_bytes;
     out->nrec = h->dirty ? 0 : h->kern.nrec;
     out->device = h->dirty ? -1 : h->device;
+    out->wave = (h->dirty || h->shape_dirty) ? 0 : (int64_t)h->sm_count * h->blocks_per_sm;
     return RMDEC_OK;
 }
 }  // namespace rmdec_host

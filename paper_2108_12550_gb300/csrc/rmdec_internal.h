@@ -45,9 +45,11 @@ struct MemberInfo {
     int warp_bytes = 0;
     int nrec = 0;  // device records per decoder
     int device = -1;
+    int64_t wave = 0;  // CTAs of the handle's own launch resident at once (valid after prepare)
 };
 // Fills *out from the handle; with prepare = true first uploads the handle's tables to the
-// current device (errors are recorded on the handle, see rmdec_last_error).
+// current device and fixes its own launch shape (errors are recorded on the handle, see
+// rmdec_last_error).
 rmdec_status member_info(rmdec_ctx* h, bool prepare, MemberInfo* out);
 
 // Grouped multi-code kernels (group_l<L>.cu), one per supported list size.

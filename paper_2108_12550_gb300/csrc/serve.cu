@@ -7,6 +7,13 @@
 // block, decoded with a single rmdec_decode launch and copied back, all on the batch's stream,
 // so copies and decodes of different batches overlap on the device. A completion event per
 // batch retires its requests and frees its arena block, which admits the next requests.
+//
+// With fuse_codes, codes that can share a grouped launch (include/rmdec_group.h: p-FHT-FSCL
+// decoders of one list size, up to 16 per family) form a family. When the oldest request is
+// smaller than one full wave of its code's own launch, the batch is the FIFO run of the
+// family's requests of that kind: they are laid out code by code in the arena and decoded by
+// one rmdec_group_decode call with one segment per code. Larger requests are batched per
+// code as without fusing.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -24,6 +31,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/rmdec.h"
+#include "../../include/rmdec_group.h"
 #include "../../include/rmdec_serve.h"
 #include "rmdec_internal.h"
 
@@ -107,8 +115,18 @@ struct rmdec_server {
     struct Code {
         rmdec_t h;
         size_t in_bpf, out_bpf;
+        int family;  // -1: decoded alone
+        int member;  // index within the family's group
+        int64_t wave = -1;  // frames that fill the GPU in the code's own launch (-1: not known yet)
+    };
+    struct Family {
+        int L = 0;
+        std::vector<int> codes;
+        rmdec_group_t grp = nullptr;
+        bool stale = true;  // group must be (re)created with the current member list
     };
     std::vector<Code> codes;
+    std::vector<Family> families;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Request*> pending;
@@ -172,12 +190,33 @@ struct rmdec_server {
             }
         if (sidx < 0) return false;
         const int code = pending.front()->code;
-        const Code& c = codes[code];
-        // FIFO run of the oldest request's code
+        const int fam = codes[code].family;
+        if (fam >= 0 && families[fam].stale) {
+            Family& F = families[fam];
+            if (F.grp) rmdec_group_destroy(F.grp);
+            F.grp = nullptr;
+            std::vector<rmdec_t> hs;
+            for (int ci : F.codes) hs.push_back(codes[ci].h);
+            if (rmdec_group_create(&F.grp, hs.data(), (int)hs.size()) != RMDEC_OK) F.grp = nullptr;
+            F.stale = false;
+        }
+        // Requests that fill the GPU on their own gain nothing from sharing a launch and would
+        // hold up the small ones batched with them: only requests below their code's wave are
+        // fused; a large oldest request starts a batch of its own code as without fusing.
+        auto small = [&](const Request* r) {
+            Code& c = codes[r->code];
+            if (c.wave < 0) {
+                rmdec_host::MemberInfo mi;
+                c.wave = rmdec_host::member_info(c.h, true, &mi) == RMDEC_OK ? mi.wave : 0;
+            }
+            return r->frames < c.wave;
+        };
+        const bool fused = fam >= 0 && families[fam].grp && small(pending.front());
+        // FIFO run of the oldest request's code (or, fused, of its family's small requests)
         std::vector<Request*> take;
         int64_t frames = 0;
         for (Request* r : pending) {
-            if (r->code != code) continue;
+            if (fused ? (codes[r->code].family != fam || !small(r)) : r->code != code) continue;
             if (frames + r->frames > cfg.max_batch_frames) break;
             take.push_back(r);
             frames += r->frames;
@@ -185,9 +224,31 @@ struct rmdec_server {
         if (take.empty()) return false;
         const double waited = std::chrono::duration<double, std::micro>(Clock::now() - take.front()->t_submit).count();
         if (frames < cfg.min_batch_frames && waited < (double)cfg.max_wait_us && !inflight.empty()) return false;
-        const size_t in_b = align256((size_t)frames * c.in_bpf), out_b = align256((size_t)frames * c.out_bpf);
+        // arena layout: per code in the batch (in order of first appearance), its requests'
+        // LLRs, then their output words
+        struct Part {
+            int code;
+            int64_t frames = 0;
+            size_t in_off = 0, out_off = 0;
+        };
+        std::vector<Part> parts;
+        for (Request* r : take) {
+            auto it = std::find_if(parts.begin(), parts.end(), [&](const Part& p) { return p.code == r->code; });
+            if (it == parts.end()) {
+                parts.push_back(Part{r->code});
+                it = parts.end() - 1;
+            }
+            it->frames += r->frames;
+        }
+        size_t bytes = 0;
+        for (Part& p : parts) {
+            p.in_off = bytes;
+            bytes += align256((size_t)p.frames * codes[p.code].in_bpf);
+            p.out_off = bytes;
+            bytes += align256((size_t)p.frames * codes[p.code].out_bpf);
+        }
         size_t off = 0;
-        if (!arena.alloc(in_b + out_b, &off)) return false;  // admission waits for memory
+        if (!arena.alloc(bytes, &off)) return false;  // admission waits for memory
         for (Request* r : take) pending.erase(std::find(pending.begin(), pending.end(), r));
         Batch* b = new Batch;
         b->code = code;
@@ -195,26 +256,44 @@ struct rmdec_server {
         b->reqs = take;
         b->frames = frames;
         b->offset = off;
-        b->bytes = in_b + out_b;
+        b->bytes = bytes;
         stream_busy[sidx] = true;
         n_batches++;
+        rmdec_group_t grp = fused ? families[fam].grp : nullptr;
         lk.unlock();
         cudaStream_t st = streams[sidx];
         uint8_t* base = static_cast<uint8_t*>(arena_ptr) + off;
-        uint32_t* dout = reinterpret_cast<uint32_t*>(base + in_b);
         bool ok = true;
-        int64_t f0 = 0;
-        for (Request* r : take) {
-            ok &= cudaMemcpyAsync(base + (size_t)f0 * c.in_bpf, r->llr, (size_t)r->frames * c.in_bpf,
+        std::vector<int64_t> at(parts.size(), 0);  // frames placed so far per part
+        std::vector<size_t> req_part(take.size());
+        std::vector<int64_t> req_at(take.size());
+        for (size_t q = 0; q < take.size(); q++) {
+            Request* r = take[q];
+            const size_t pi = std::find_if(parts.begin(), parts.end(), [&](const Part& p) { return p.code == r->code; }) - parts.begin();
+            req_part[q] = pi;
+            req_at[q] = at[pi];
+            const Code& c = codes[r->code];
+            ok &= cudaMemcpyAsync(base + parts[pi].in_off + (size_t)at[pi] * c.in_bpf, r->llr, (size_t)r->frames * c.in_bpf,
                                   cudaMemcpyHostToDevice, st) == cudaSuccess;
-            f0 += r->frames;
+            at[pi] += r->frames;
         }
-        ok &= rmdec_decode(c.h, base, frames, dout, st) == RMDEC_OK;
-        f0 = 0;
-        for (Request* r : take) {
-            ok &= cudaMemcpyAsync(r->out, reinterpret_cast<uint8_t*>(dout) + (size_t)f0 * c.out_bpf,
-                                  (size_t)r->frames * c.out_bpf, cudaMemcpyDeviceToHost, st) == cudaSuccess;
-            f0 += r->frames;
+        if (grp) {
+            std::vector<rmdec_segment> segs;
+            for (const Part& p : parts)
+                segs.push_back(rmdec_segment{codes[p.code].member, base + p.in_off, p.frames,
+                                             reinterpret_cast<uint32_t*>(base + p.out_off)});
+            ok &= rmdec_group_decode(grp, segs.data(), (int)segs.size(), st) == RMDEC_OK;
+        } else {
+            for (const Part& p : parts)
+                ok &= rmdec_decode(codes[p.code].h, base + p.in_off, p.frames, reinterpret_cast<uint32_t*>(base + p.out_off),
+                                   st) == RMDEC_OK;
+        }
+        for (size_t q = 0; q < take.size(); q++) {
+            Request* r = take[q];
+            const Part& p = parts[req_part[q]];
+            const Code& c = codes[r->code];
+            ok &= cudaMemcpyAsync(r->out, base + p.out_off + (size_t)req_at[q] * c.out_bpf, (size_t)r->frames * c.out_bpf,
+                                  cudaMemcpyDeviceToHost, st) == cudaSuccess;
         }
         cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
         cudaEventRecord(b->ev, st);
@@ -252,7 +331,7 @@ rmdec_status rmdec_server_create(rmdec_server_t* out, const rmdec_server_config*
     }
     *out = nullptr;
     if (cfg->n_streams < 1 || cfg->n_streams > 16 || cfg->arena_bytes <= 0 || cfg->max_batch_frames < 1 ||
-        cfg->min_batch_frames < 0 || cfg->max_wait_us < 0) {
+        cfg->min_batch_frames < 0 || cfg->max_wait_us < 0 || cfg->fuse_codes < 0 || cfg->fuse_codes > 1) {
         g_server_error = "bad server configuration";
         return RMDEC_EINVAL;
     }
@@ -283,9 +362,25 @@ rmdec_status rmdec_server_add_decoder(rmdec_server_t s, rmdec_t h, int* code_id)
     if (!s || !h || !code_id) return RMDEC_EINVAL;
     int n = 0, k = 0;
     if (rmdec_info(h, &n, &k, nullptr) != RMDEC_OK) return s->fail(RMDEC_EINVAL, "bad decoder handle");
+    rmdec_host::MemberInfo mi;
+    if (rmdec_host::member_info(h, false, &mi) != RMDEC_OK) return s->fail(RMDEC_EINVAL, "bad decoder handle");
     std::lock_guard<std::mutex> g(s->mu);
-    s->codes.push_back({h, (size_t)n * rmdec_host::llr_elem_bytes_of(h), (size_t)((k + 31) / 32) * 4});
-    *code_id = (int)s->codes.size() - 1;
+    const int id = (int)s->codes.size();
+    int fam = -1, member = 0;
+    if (s->cfg.fuse_codes && mi.algo == 0 && (mi.L == 1 || mi.L == 2 || mi.L == 4)) {
+        for (int f = 0; f < (int)s->families.size(); f++)
+            if (s->families[f].L == mi.L && s->families[f].codes.size() < 16) fam = f;
+        if (fam < 0) {
+            s->families.emplace_back();
+            fam = (int)s->families.size() - 1;
+            s->families[fam].L = mi.L;
+        }
+        member = (int)s->families[fam].codes.size();
+        s->families[fam].codes.push_back(id);
+        s->families[fam].stale = true;
+    }
+    s->codes.push_back({h, (size_t)n * rmdec_host::llr_elem_bytes_of(h), (size_t)((k + 31) / 32) * 4, fam, member});
+    *code_id = id;
     return RMDEC_OK;
 }
 
@@ -374,6 +469,8 @@ void rmdec_server_destroy(rmdec_server_t s) {
     if (s->worker.joinable()) s->worker.join();
     for (auto& kv : s->requests) delete kv.second;
     for (auto& st : s->streams) cudaStreamDestroy(st);
+    for (auto& f : s->families)
+        if (f.grp) rmdec_group_destroy(f.grp);
     if (s->arena_ptr) cudaFree(s->arena_ptr);
     delete s;
 }

@@ -100,6 +100,26 @@ def test_real_valued_group_equals_separate_decodes():
     grp.close()
 
 
+@pytest.mark.parametrize("split", [0, -1, 1000])
+def test_large_segments_in_own_launches_give_the_same_bits(split):
+    decs = [pkg.Decoder(7, 2, 8, 4, perm_seed=1, dtype="i8"), pkg.Decoder(9, 2, 20, 4, perm_seed=2),
+            pkg.Decoder(8, 2, 8, 4, perm_seed=3)]
+    grp = pkg.Group(decs)
+    grp.set_split(split)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(17)
+    segs = []
+    for di, nf in [(0, 5000), (1, 300), (2, 1200), (0, 40), (1, 1600)]:
+        d = decs[di]
+        _, llr = I.make_frames_torch(d.m, d.r, nf, 2.5, gen)
+        x = torch.clamp(torch.round(llr / 0.25), -127, 127).to(torch.int8) if di == 0 else llr
+        segs.append((di, x.contiguous(), None))
+    outs = grp.decode(segs)
+    for (di, x, _), out in zip(segs, outs):
+        assert torch.equal(out, decs[di].decode(x))
+    grp.close()
+
+
 def test_long_segment_lists_are_split_over_launches():
     decs = [pkg.Decoder(5, 2, 4, 2, perm_seed=1, dtype="i8"), pkg.Decoder(7, 2, 3, 2, perm_seed=2, dtype="i8")]
     grp = pkg.Group(decs)

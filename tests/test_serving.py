@@ -10,11 +10,12 @@ from paper_2108_12550_gb300 import inputs as I
 
 torch = pytest.importorskip("torch")
 
-MIX = [  # (m, r, P, L, dtype)
-    (7, 2, 8, 4, "i8"),
-    (8, 2, 8, 4, "f32"),
-    (9, 2, 20, 4, "f32"),
-    (9, 3, 8, 4, "i8"),
+MIX = [  # (m, r, P, L, dtype, algo)
+    (7, 2, 8, 4, "i8", "pfht"),
+    (8, 2, 8, 4, "f32", "pfht"),
+    (9, 2, 20, 4, "f32", "pfht"),
+    (9, 3, 8, 4, "i8", "pfht"),
+    (7, 2, 16, 1, "f32", "autssc"),  # never fused: decoded by its own launches
 ]
 
 
@@ -23,7 +24,7 @@ def _requests(n, seed):
     reqs = []
     for q in range(n):
         c = int(rng.integers(len(MIX)))
-        m, r, P, L, dt = MIX[c]
+        m, r, P, L, dt, _ = MIX[c]
         nf = int(np.exp(rng.uniform(0, np.log(300))))
         fr = I.make_frames(m, r, nf, float(rng.uniform(2, 5)), seed=seed * 1000 + q)
         x = I.quantize_i8(fr["llr"]) if dt == "i8" else fr["llr"].astype(np.float32)
@@ -32,13 +33,15 @@ def _requests(n, seed):
 
 
 @pytest.mark.gpu
-def test_mixed_requests_match_alone_decoding():
-    decs = [pkg.Decoder(m, r, P, L, perm_seed=11 + i, dtype=dt) for i, (m, r, P, L, dt) in enumerate(MIX)]
-    reqs = _requests(120, seed=3)
+@pytest.mark.parametrize("fuse", [False, True])
+def test_mixed_requests_match_alone_decoding(fuse):
+    decs = [pkg.Decoder(m, r, P, L, perm_seed=11 + i, dtype=dt, algo=algo)
+            for i, (m, r, P, L, dt, algo) in enumerate(MIX)]
+    reqs = _requests(120, seed=3 + fuse)
     # alone: one decode call per request
     alone = [decs[c].decode(x.cuda()).cpu() for c, x in reqs]
     srv = pkg.Server(n_streams=4, arena_bytes=64 << 20, max_batch_frames=4096, min_batch_frames=256,
-                     max_wait_us=200)
+                     max_wait_us=200, fuse_codes=fuse)
     ids = [srv.add_decoder(d) for d in decs]
     outs = [torch.zeros((x.shape[0], decs[c].kw), dtype=torch.int32).pin_memory() for c, x in reqs]
     rids = [None] * len(reqs)
@@ -95,6 +98,8 @@ def test_server_configuration_is_validated_on_the_host():
 
     h = ctypes.c_void_p()
     bad = pkg._ServerConfig(0, 1 << 20, 16, 0, 0)
+    assert lib.rmdec_server_create(ctypes.byref(h), ctypes.byref(bad)) == pkg.EINVAL
+    bad = pkg._ServerConfig(2, 1 << 20, 16, 0, 0, 2)  # fuse_codes is 0 or 1
     assert lib.rmdec_server_create(ctypes.byref(h), ctypes.byref(bad)) == pkg.EINVAL
     assert lib.rmdec_server_create(ctypes.byref(h), None) == pkg.EINVAL
     if not torch.cuda.is_available():
