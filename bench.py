@@ -426,7 +426,8 @@ def main():
         "dtype": args.dtype, "data": "synthetic",
         "config": {"workload": args.workload, "m": m, "r": r, "P": P, "L": L, "n": n, "k": k,
                    "ebn0_db": ebn0, "frames_per_step": nf, "l2": "inputs larger than L2 "
-                   f"({llr_np.nbytes / 2**20:.0f} MiB of LLRs per step)", "parallelism": f"replicas{world}"},
+                   f"({llr_np.nbytes / 2**20:.0f} MiB of LLRs per step)", "parallelism": f"replicas{world}",
+                   "launch": dict(zip(("warps_per_cta", "ctas_per_sm"), dec.get_tuning()))},
         "info_gbit_s": value * k / 1e9,
         "fer_of_timed_batch": fer,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",

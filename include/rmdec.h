@@ -129,9 +129,14 @@ rmdec_status rmdec_submit(rmdec_t h, const void *llr_dev, int64_t n_frames, uint
  * RMDEC_ETIMEDOUT if the wait expired, RMDEC_EINVAL for an unknown ticket. */
 rmdec_status rmdec_poll(rmdec_t h, uint64_t ticket, int64_t timeout_us);
 
-/* Launch shape: warps per CTA (1..4; the decoders of a frame are split across a CTA's warps)
- * and a cap on resident CTAs per SM (0 = the occupancy limit). Takes effect on the next
- * decode. Not part of the paper's method: it only changes scheduling, never results. */
+/* Launch shape: warps per CTA (1..20, at most P; Aut-SSC handles use at most 4; the decoders
+ * of a frame are split across a CTA's warps) and a cap on resident CTAs per SM (0 = the
+ * occupancy limit); 0 warps = the default: the most resident warps per SM, then warps that
+ * split the P decoders evenly, then two or more decoders per warp and two or more CTAs per
+ * SM, then the widest CTA for m = 9 and the narrowest below (see rmdec_autotune). A shape
+ * whose shared memory does not fit fails the next decode with RMDEC_EINVAL. Takes effect on
+ * the next decode. Not part of the paper's method: it only changes scheduling, never
+ * results. */
 rmdec_status rmdec_set_tuning(rmdec_t h, int warps_per_cta, int ctas_per_sm);
 rmdec_status rmdec_get_tuning(rmdec_t h, int *warps_per_cta, int *ctas_per_sm);
 

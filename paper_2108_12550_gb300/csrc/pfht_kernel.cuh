@@ -27,7 +27,8 @@
 namespace rmdec_dev {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kRec = 11;  // uint16 per permutation record: [c_0..c_9, b]
+constexpr int kRec = 11;      // uint16 per permutation record: [c_0..c_9, b]
+constexpr int kMaxWarps = 20; // widest pfht_kernel CTA (its register budget: 96 per thread)
 
 enum InType { IN_F32 = 0, IN_I8 = 1, IN_F16 = 2, IN_I16 = 3 };
 
@@ -948,7 +949,7 @@ __device__ __forceinline__ void decode_frame(const FrameJob& j, const FrameSmem&
 }
 
 template <int M, int R, int L>
-__global__ void __launch_bounds__(128, 5) pfht_kernel(LaunchArgs args) {
+__global__ void __launch_bounds__(32 * kMaxWarps, 1) pfht_kernel(LaunchArgs args) {
     using C = Cfg<M, R, L>;
     extern __shared__ __align__(16) uint8_t smem[];
     const int rec_elems = args.P * C::NREC * kRec;

@@ -9,6 +9,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <thread>
 #include <vector>
 
@@ -232,6 +233,10 @@ rmdec_status ensure_device(rmdec_ctx* h) {
     return RMDEC_OK;
 }
 
+// Widest CTA a handle's kernel accepts: pfht_kernel is built for up to kMaxWarps warps, and
+// more warps than decoders would idle.
+int max_warps_per_cta(const rmdec_ctx* h) { return h->algo == 0 ? std::min(h->P, rmdec_dev::kMaxWarps) : 4; }
+
 // Launch shape: warps per CTA (decoders of a frame split across warps) and resident CTAs.
 rmdec_status configure_shape(rmdec_ctx* h) {
     if (!h->shape_dirty) return RMDEC_OK;
@@ -242,7 +247,7 @@ rmdec_status configure_shape(rmdec_ctx* h) {
     // launch in any order
     if ((e = cudaFuncSetAttribute(h->kern.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)) != cudaSuccess)
         return h->cuda_fail(e, "cudaFuncSetAttribute");
-    const int wmax = h->algo == 0 ? std::min(h->P, 4) : 4;
+    const int wmax = max_warps_per_cta(h);
     auto smem_for = [&](int W) { return (size_t)h->kern.fixed_bytes(h->P, h->k, W) + 16 + (size_t)W * h->kern.warp_bytes; };
     auto occ_for = [&](int W) {
         int o = 0;
@@ -254,15 +259,27 @@ rmdec_status configure_shape(rmdec_ctx* h) {
     if (!W)
         if (const char* s = getenv("RMDEC_WARPS")) W = atoi(s);
     if (!W) {
-        // default: the most resident warps per SM, then the widest CTA
-        int best = -1;
-        for (int c = 1; c <= wmax; c++) {
-            const int warps = occ_for(c) * c;
-            if (warps >= best) {
-                best = warps;
+        // default: the most resident warps per SM; among equals, warps that split the P
+        // decoders evenly, then at least two decoders per warp and at least two CTAs per SM
+        // (a lone decoder per warp, or a lone CTA, leaves the SM idle at every frame
+        // boundary). Last, the CTA width: the m = 9 trees compile to 80-380 KB of straight-line
+        // code, more than the instruction caches hold, and run fastest in the widest CTA,
+        // whose warps walk the tree's code together; smaller codes fit and run fastest in
+        // the narrowest CTAs, which never wait for each other.
+        const bool wide = h->m >= 9;
+        auto score = [&](int c) {
+            const int occ = occ_for(c);
+            const bool even = h->algo != 0 || h->P % c == 0;
+            const bool two_each = h->algo != 0 || h->P >= 2 * c;
+            return std::make_tuple(occ * c, even, two_each, occ >= 2, wide ? c : -c);
+        };
+        auto best = score(1);
+        W = 1;
+        for (int c = 2; c <= wmax; c++)
+            if (score(c) > best) {
+                best = score(c);
                 W = c;
             }
-        }
     }
     W = std::max(1, std::min(wmax, W));
     h->warps = W;
@@ -542,8 +559,8 @@ rmdec_status rmdec_poll(rmdec_t h, uint64_t ticket, int64_t timeout_us) {
 
 rmdec_status rmdec_set_tuning(rmdec_t h, int warps_per_cta, int ctas_per_sm) {
     if (!h) return RMDEC_EINVAL;
-    if (warps_per_cta < 0 || warps_per_cta > 4 || ctas_per_sm < 0 || ctas_per_sm > 32)
-        return h->fail(RMDEC_EINVAL, "warps_per_cta must be 0..4 and ctas_per_sm 0..32");
+    if (warps_per_cta < 0 || warps_per_cta > rmdec_dev::kMaxWarps || ctas_per_sm < 0 || ctas_per_sm > 32)
+        return h->fail(RMDEC_EINVAL, "warps_per_cta must be 0..%d and ctas_per_sm 0..32", rmdec_dev::kMaxWarps);
     h->req_warps = warps_per_cta;
     h->req_ctas = ctas_per_sm;
     h->shape_dirty = true;
@@ -585,7 +602,7 @@ rmdec_status rmdec_autotune(rmdec_t h, int64_t n_frames, const char* cache_path,
                 }
             fclose(f);
             if (found) {
-                h->req_warps = std::max(0, std::min(4, fw));
+                h->req_warps = std::max(0, std::min(rmdec_dev::kMaxWarps, fw));
                 h->req_ctas = std::max(0, std::min(32, fc));
                 h->shape_dirty = true;
                 return configure_shape(h);
@@ -624,7 +641,7 @@ rmdec_status rmdec_autotune(rmdec_t h, int64_t n_frames, const char* cache_path,
     cudaEventCreate(&e1);
     float best_ms = 1e30f;
     int best_w = 0;
-    const int wmax = h->algo == 0 ? std::min(4, h->P) : 4;
+    const int wmax = max_warps_per_cta(h);
     for (int w = 1; w <= wmax; w++) {
         h->req_warps = w;
         h->req_ctas = 0;

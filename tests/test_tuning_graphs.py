@@ -13,20 +13,21 @@ torch = pytest.importorskip("torch")
 
 def test_tuning_arguments_are_validated():
     d = pkg.Decoder(9, 2, 20, 4)
-    for bad in [(5, 0), (-1, 0), (2, 33)]:
+    for bad in [(21, 0), (-1, 0), (2, 33)]:
         with pytest.raises(pkg.RmdecError):
             d.set_tuning(*bad)
     d.set_tuning(2, 1)
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("m,r,P,L", [(9, 2, 20, 4), (9, 3, 16, 8), (5, 2, 4, 2)])
-def test_every_launch_shape_gives_identical_results(m, r, P, L):
+@pytest.mark.parametrize("m,r,P,L,ws", [(9, 2, 20, 4, (1, 2, 4, 7, 10, 20)), (9, 3, 16, 8, (1, 2, 4, 8)),
+                                        (5, 2, 4, 2, (1, 2, 4, 16))])
+def test_every_launch_shape_gives_identical_results(m, r, P, L, ws):
     fr = I.make_frames(m, r, 1000, 2.5, seed=4)
     x = torch.from_numpy(fr["llr"].astype(np.float32)).cuda()
     d = pkg.Decoder(m, r, P, L, perm_seed=3)
     outs = []
-    for w in (1, 2, 4):
+    for w in ws:
         for c in (0, 1):
             d.set_tuning(w, c)
             outs.append(d.decode(x).cpu())
@@ -39,7 +40,7 @@ def test_autotune_and_cache(tmp_path):
     cache = str(tmp_path / "tune.txt")
     d = pkg.Decoder(9, 2, 20, 4, perm_seed=1)
     w, c = d.autotune(n_frames=8192, cache_path=cache)
-    assert 1 <= w <= 4 and c >= 1
+    assert 1 <= w <= 20 and c >= 1
     lines = open(cache).read().split("\n")
     assert len([l for l in lines if l.strip()]) == 1
     d2 = pkg.Decoder(9, 2, 20, 4, perm_seed=2)
