@@ -52,15 +52,7 @@ def _peaks():
 
 def _frames(m, r, nf, ebn0, seed, chunk=1 << 16):
     """Seeded BPSK/AWGN frames (FP32 LLRs) and their messages, generated in chunks."""
-    n, k = I.rm_dims(m, r)
-    llr = np.empty((nf, n), dtype=np.float32)
-    u = np.empty((nf, k), dtype=np.uint8)
-    for c0 in range(0, nf, chunk):
-        c1 = min(nf, c0 + chunk)
-        fr = I.make_frames(m, r, c1 - c0, ebn0, seed=seed * 1000003 + c0)
-        llr[c0:c1] = fr["llr"]
-        u[c0:c1] = fr["u"]
-    return llr, u
+    return I.make_frames_chunked(m, r, nf, ebn0, seed, chunk)
 
 
 class Clocks:
@@ -256,51 +248,68 @@ PAPER_FER = {"p-FHT-FSCL-4-20": {1.0: 9.80e-3, 1.5: 2.11e-3, 2.0: 2.99e-4, 2.5: 
 
 
 def run_fer_sweep(args):
-    """FER of p-FHT-FSCL-4-20 and Aut-SSC-512 on the same RM(2,9) frames, generated on the GPU
-    in chunks, with decoding time per point."""
+    """FER of p-FHT-FSCL-4-20 (FP32, FP16 and INT8 LLRs) and Aut-SSC-512 on the same RM(2,9)
+    frames, generated on the GPU in chunks, with decoding time per point."""
     import torch
 
     import paper_2108_12550_gb300 as pkg
 
     m, r, k = 9, 2, 46
     pf = pkg.Decoder(m, r, 20, 4, perm_seed=1)
+    pf16 = pkg.Decoder(m, r, 20, 4, perm_seed=1, dtype="f16")
+    pf8 = pkg.Decoder(m, r, 20, 4, perm_seed=1, dtype="i8")
     ssc = pkg.Decoder(m, r, 512, algo="autssc", perm_seed=1)
     gen = torch.Generator(device="cuda")
     gen.manual_seed(2108)
     chunk = 1 << 18
     out = torch.empty((chunk, 2), dtype=torch.int32, device="cuda")
+    ref_bits = torch.empty((chunk, 2), dtype=torch.int32, device="cuda")
+    runs = [("p-FHT-FSCL-4-20", pf, lambda x: x), ("p-FHT-FSCL-4-20 FP16 LLRs", pf16, lambda x: x.half()),
+            ("p-FHT-FSCL-4-20 INT8 LLRs", pf8, lambda x: torch.clamp(torch.round(x / 0.25), -127, 127).to(torch.int8)),
+            ("Aut-SSC-512", ssc, lambda x: x)]
     points = []
     for eb in args.ebn0:
         n_pf = args.sweep_frames
         n_ssc = min(args.sweep_frames, args.ssc_frames)
-        err = {"p-FHT-FSCL-4-20": 0, "Aut-SSC-512": 0}
-        t_dec = {"p-FHT-FSCL-4-20": 0.0, "Aut-SSC-512": 0.0}
+        lims = {name: (n_ssc if name == "Aut-SSC-512" else n_pf) for name, _, _ in runs}
+        err = {name: 0 for name, _, _ in runs}
+        differ = {name: 0 for name, _, _ in runs}  # decisions other than the FP32 decoder's
+        t_dec = {name: 0.0 for name, _, _ in runs}
         done = 0
         while done < n_pf:
             f = min(chunk, n_pf - done)
             u, llr = I.make_frames_torch(m, r, f, eb, gen)
             unpack = lambda w: ((w.view(-1, 2, 1) >> torch.arange(32, device="cuda")) & 1).view(-1, 64)[:, :k]
-            for name, dec, lim in (("p-FHT-FSCL-4-20", pf, n_pf), ("Aut-SSC-512", ssc, n_ssc)):
-                if done >= lim:
+            for name, dec, conv in runs:
+                if done >= lims[name]:
                     continue
-                g = min(f, lim - done)
+                g = min(f, lims[name] - done)
+                xin = conv(llr[:g]).contiguous()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
-                dec.decode(llr[:g], out[:g])
+                dec.decode(xin, out[:g])
                 e1.record()
                 torch.cuda.synchronize()
                 t_dec[name] += e0.elapsed_time(e1) * 1e-3
                 err[name] += int(torch.any(unpack(out[:g]).to(torch.uint8) != u[:g], dim=1).sum().item())
+                if name == "p-FHT-FSCL-4-20":
+                    ref_bits[:g].copy_(out[:g])
+                elif name.startswith("p-FHT"):
+                    differ[name] += int(torch.any(out[:g] != ref_bits[:g], dim=1).sum().item())
             done += f
         pt = {"ebn0_db": eb}
-        for name, n in (("p-FHT-FSCL-4-20", n_pf), ("Aut-SSC-512", n_ssc)):
+        for name, _, _ in runs:
+            n = lims[name]
             pt[name] = {"frames": n, "errors": err[name], "fer": err[name] / n,
-                        "frames_per_s": n / t_dec[name] if t_dec[name] else None,
-                        "paper_fer": PAPER_FER[name].get(eb)}
+                        "frames_per_s": n / t_dec[name] if t_dec[name] else None}
+            if name in PAPER_FER:
+                pt[name]["paper_fer"] = PAPER_FER[name].get(eb)
+            if name.startswith("p-FHT") and name != "p-FHT-FSCL-4-20":
+                pt[name]["decisions_differing_from_fp32"] = differ[name] / n
         points.append(pt)
         print(json.dumps(pt), flush=True)
-    print(json.dumps({"metric": "FER RM(2,9): p-FHT-FSCL-4-20 vs Aut-SSC-512 on the same frames", "points": points,
-                      "data": "synthetic BPSK/AWGN frames generated on the GPU"}), flush=True)
+    print(json.dumps({"metric": "FER RM(2,9): p-FHT-FSCL-4-20 (FP32/FP16/INT8 LLRs) vs Aut-SSC-512 on the same frames",
+                      "points": points, "data": "synthetic BPSK/AWGN frames generated on the GPU"}), flush=True)
 
 
 def main():

@@ -213,6 +213,21 @@ def ssc_perm_table(m: int, P_ssc: int, seed: int) -> np.ndarray:
     return np.stack([sample_ga(m, seed, SSC_STREAM, q) for q in range(P_ssc)])
 
 
+def make_frames_chunked(m: int, r: int, n_frames: int, ebn0_db: float, seed: int, chunk: int = 1 << 16):
+    """Large batches of make_frames, generated in chunks of `chunk` frames, chunk c0 with seed
+    seed * 1000003 + c0 (the full-size benchmark batches). Returns (llr float32 [F,N],
+    u uint8 [F,K])."""
+    n, k = rm_dims(m, r)
+    llr = np.empty((n_frames, n), dtype=np.float32)
+    u = np.empty((n_frames, k), dtype=np.uint8)
+    for c0 in range(0, n_frames, chunk):
+        c1 = min(n_frames, c0 + chunk)
+        fr = make_frames(m, r, c1 - c0, ebn0_db, seed=seed * 1000003 + c0)
+        llr[c0:c1] = fr["llr"]
+        u[c0:c1] = fr["u"]
+    return llr, u
+
+
 def make_frames_torch(m: int, r: int, n_frames: int, ebn0_db: float, generator, device="cuda"):
     """The same transmitter and channel as make_frames, on a torch device (for sweeps whose
     frames are too many to stage from the host): uniform messages, x = u G^{(x)m}, BPSK over

@@ -1,0 +1,42 @@
+"""Decision-mismatch rates of the input precisions against the FP64 oracle.
+
+The same seeded frames at the operating points are decoded by the GPU from FP32, FP16 and
+INT8 (step 0.25, saturated at +-127) LLRs and by the FP64 oracle from the exact channel
+LLRs. FP32 decides like FP64 except at near-ties; the quantised inputs change the metric
+itself, so their words may differ wherever the quantisation moves a decision, and the test
+bounds those rates (the measured values are printed and stated in the design notes).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle as O  # noqa: E402
+import paper_2108_12550_gb300 as pkg  # noqa: E402
+from paper_2108_12550_gb300 import inputs as I  # noqa: E402
+
+# (m, r, P, L, Eb/N0, frames, largest tolerated mismatch rate per input type)
+POINTS = [
+    (9, 2, 20, 4, 2.25, 3000, {"f32": 0.01, "f16": 0.03, "i8": 0.10}),
+    (9, 3, 16, 8, 4.0, 600, {"f32": 0.01, "f16": 0.03, "i8": 0.10}),
+]
+
+
+@pytest.mark.parametrize("m,r,P,L,eb,nf,bound", POINTS, ids=["rm29_p20_l4", "rm39_p16_l8"])
+def test_mismatch_rates_vs_fp64_oracle(m, r, P, L, eb, nf, bound):
+    fr = I.make_frames(m, r, nf, eb, seed=4242)
+    perms = I.perm_table(m, r, P, L, seed=1)
+    ref = O.decode(m, r, P, L, perms, fr["llr"])
+    inputs = {"f32": fr["llr"].astype(np.float32), "f16": I.to_f16(fr["llr"]), "i8": I.quantize_i8(fr["llr"])}
+    rates = {}
+    for dt, x in inputs.items():
+        dec = pkg.Decoder(m, r, P, L, dtype=dt, perms=perms)
+        out = dec.decode(torch.from_numpy(x).cuda()).cpu().numpy()
+        info = pkg.unpack_bits(out, dec.k)
+        rates[dt] = float(np.mean(np.any(info != ref["info"], axis=1)))
+        fer = float(np.mean(np.any(info != fr["u"], axis=1)))
+        print(f"RM({r},{m}) P={P} L={L} {eb} dB {dt}: decisions differing from FP64 {rates[dt]:.4%} "
+              f"(FER {fer:.4%}, FP64 oracle FER {np.mean(np.any(ref['info'] != fr['u'], axis=1)):.4%})")
+    for dt, b in bound.items():
+        assert rates[dt] <= b, (dt, rates[dt])
