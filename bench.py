@@ -260,13 +260,21 @@ def run_fer_sweep(args):
     pf8 = pkg.Decoder(m, r, 20, 4, perm_seed=1, dtype="i8")
     ssc = pkg.Decoder(m, r, 512, algo="autssc", perm_seed=1)
     gen = torch.Generator(device="cuda")
-    gen.manual_seed(2108)
     chunk = 1 << 18
     out = torch.empty((chunk, 2), dtype=torch.int32, device="cuda")
     ref_bits = torch.empty((chunk, 2), dtype=torch.int32, device="cuda")
     runs = [("p-FHT-FSCL-4-20", pf, lambda x: x), ("p-FHT-FSCL-4-20 FP16 LLRs", pf16, lambda x: x.half()),
             ("p-FHT-FSCL-4-20 INT8 LLRs", pf8, lambda x: torch.clamp(torch.round(x / 0.25), -127, 127).to(torch.int8)),
             ("Aut-SSC-512", ssc, lambda x: x)]
+    # Chunk c of point Eb/N0 draws its frames from its own seed, so chunks are independent and
+    # a sweep can stop and resume: --checkpoint keeps one JSON line per finished chunk.
+    done_chunks = {}
+    if args.checkpoint and os.path.exists(args.checkpoint):
+        with open(args.checkpoint) as fh:
+            for line in fh:
+                rec = json.loads(line)
+                done_chunks[(rec["ebn0_db"], rec["chunk"])] = rec
+    ckpt = open(args.checkpoint, "a") if args.checkpoint else None
     points = []
     for eb in args.ebn0:
         n_pf = args.sweep_frames
@@ -275,28 +283,37 @@ def run_fer_sweep(args):
         err = {name: 0 for name, _, _ in runs}
         differ = {name: 0 for name, _, _ in runs}  # decisions other than the FP32 decoder's
         t_dec = {name: 0.0 for name, _, _ in runs}
-        done = 0
-        while done < n_pf:
+        for ci, done in enumerate(range(0, n_pf, chunk)):
             f = min(chunk, n_pf - done)
-            u, llr = I.make_frames_torch(m, r, f, eb, gen)
-            unpack = lambda w: ((w.view(-1, 2, 1) >> torch.arange(32, device="cuda")) & 1).view(-1, 64)[:, :k]
-            for name, dec, conv in runs:
-                if done >= lims[name]:
-                    continue
-                g = min(f, lims[name] - done)
-                xin = conv(llr[:g]).contiguous()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                dec.decode(xin, out[:g])
-                e1.record()
-                torch.cuda.synchronize()
-                t_dec[name] += e0.elapsed_time(e1) * 1e-3
-                err[name] += int(torch.any(unpack(out[:g]).to(torch.uint8) != u[:g], dim=1).sum().item())
-                if name == "p-FHT-FSCL-4-20":
-                    ref_bits[:g].copy_(out[:g])
-                elif name.startswith("p-FHT"):
-                    differ[name] += int(torch.any(out[:g] != ref_bits[:g], dim=1).sum().item())
-            done += f
+            rec = done_chunks.get((eb, ci))
+            if rec is None or rec["frames"] != f:
+                gen.manual_seed(2108 * 1000003 + int(round(eb * 1000)) * 65537 + ci)
+                u, llr = I.make_frames_torch(m, r, f, eb, gen)
+                unpack = lambda w: ((w.view(-1, 2, 1) >> torch.arange(32, device="cuda")) & 1).view(-1, 64)[:, :k]
+                rec = {"ebn0_db": eb, "chunk": ci, "frames": f, "errors": {}, "differ": {}, "seconds": {}}
+                for name, dec, conv in runs:
+                    if done >= lims[name]:
+                        continue
+                    g = min(f, lims[name] - done)
+                    xin = conv(llr[:g]).contiguous()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    dec.decode(xin, out[:g])
+                    e1.record()
+                    torch.cuda.synchronize()
+                    rec["seconds"][name] = e0.elapsed_time(e1) * 1e-3
+                    rec["errors"][name] = int(torch.any(unpack(out[:g]).to(torch.uint8) != u[:g], dim=1).sum().item())
+                    if name == "p-FHT-FSCL-4-20":
+                        ref_bits[:g].copy_(out[:g])
+                    elif name.startswith("p-FHT"):
+                        rec["differ"][name] = int(torch.any(out[:g] != ref_bits[:g], dim=1).sum().item())
+                if ckpt:
+                    ckpt.write(json.dumps(rec) + "\n")
+                    ckpt.flush()
+            for name in rec["errors"]:
+                err[name] += rec["errors"][name]
+                t_dec[name] += rec["seconds"][name]
+                differ[name] += rec["differ"].get(name, 0)
         pt = {"ebn0_db": eb}
         for name, _, _ in runs:
             n = lims[name]
@@ -308,6 +325,8 @@ def run_fer_sweep(args):
                 pt[name]["decisions_differing_from_fp32"] = differ[name] / n
         points.append(pt)
         print(json.dumps(pt), flush=True)
+    if ckpt:
+        ckpt.close()
     print(json.dumps({"metric": "FER RM(2,9): p-FHT-FSCL-4-20 (FP32/FP16/INT8 LLRs) vs Aut-SSC-512 on the same frames",
                       "points": points, "data": "synthetic BPSK/AWGN frames generated on the GPU"}), flush=True)
 
@@ -323,6 +342,7 @@ def main():
                     help="FER sweep: Eb/N0 points (dB)")
     ap.add_argument("--sweep-frames", type=int, default=1 << 22, help="FER sweep: frames per point")
     ap.add_argument("--ssc-frames", type=int, default=1 << 20, help="FER sweep: Aut-SSC frames per point")
+    ap.add_argument("--checkpoint", default=None, help="fer_sweep: JSON-lines file of finished chunks (resume)")
     ap.add_argument("--requests", type=int, default=2000, help="serving mix: requests in the trace")
     ap.add_argument("--rate", type=float, default=8000.0, help="serving mix: Poisson arrivals per second")
     ap.add_argument("--streams", type=int, default=4, help="serving mix: server CUDA streams")

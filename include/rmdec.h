@@ -32,6 +32,7 @@ typedef enum {
     RMDEC_EBUSY = -4,       /* rmdec_poll: the ticket's work has not finished yet */
     RMDEC_ETIMEDOUT = -5,   /* rmdec_poll: still running when the timeout expired */
     RMDEC_EDEVICE = -6,     /* no usable CUDA device */
+    RMDEC_ECANCELED = -7,   /* rmdec_server_poll: the request was cancelled before admission */
 } rmdec_status;
 
 /* LLR element type of the input frames.
@@ -156,6 +157,12 @@ rmdec_status rmdec_graph_create(rmdec_t h, const void *llr_host, int64_t n_frame
 /* Enqueues one replay on `stream` (asynchronous; synchronise the stream to read the bits). */
 rmdec_status rmdec_graph_launch(rmdec_graph_t g, void *stream);
 void rmdec_graph_destroy(rmdec_graph_t g);
+
+/* Test hook for failure handling: the next n device allocations made by this library
+ * (decoder tables, staging, graph and autotuning buffers, server arenas) fail as if the
+ * device were out of memory, so that callers can exercise their RMDEC_ENOMEM paths without
+ * exhausting a shared GPU; n = 0 disarms it. Process-wide. Not part of the paper's method. */
+rmdec_status rmdec_debug_fail_device_allocs(int64_t n);
 
 /* Per-thread description of the last failure on this handle (or of the last failed create
  * when h is NULL). Never NULL; valid until the next call on the same handle. */

@@ -45,6 +45,7 @@ typedef struct {
     int64_t queued, in_flight;       /* requests waiting for admission / admitted, not done */
     double latency_p50_us, latency_p99_us, latency_max_us;  /* over completed requests */
     double busy_seconds;             /* wall time from first submit to last completion */
+    int64_t cancelled;               /* requests cancelled before admission */
 } rmdec_server_stats;
 
 /* Creates a server on the current CUDA device; allocates the arena and the streams and starts
@@ -64,8 +65,13 @@ rmdec_status rmdec_server_submit(rmdec_server_t s, int code_id, const void *llr_
 /* Waits up to timeout_us (0 = check) for a request: RMDEC_OK when its bits are in the host
  * buffer (the request is retired; *latency_us, if not NULL, receives submit-to-completion
  * time), RMDEC_EBUSY / RMDEC_ETIMEDOUT otherwise, RMDEC_EINVAL for an unknown id,
- * RMDEC_ECUDA if its batch failed. */
+ * RMDEC_ECUDA if its batch failed, RMDEC_ECANCELED (retired) if it was cancelled. */
 rmdec_status rmdec_server_poll(rmdec_server_t s, uint64_t request, int64_t timeout_us, double *latency_us);
+
+/* Cancels a request that has not been admitted yet: it will never touch its buffers, and
+ * rmdec_server_poll retires it with RMDEC_ECANCELED. RMDEC_EBUSY if it was already admitted
+ * (its batch completes normally), RMDEC_EINVAL for an unknown id. */
+rmdec_status rmdec_server_cancel(rmdec_server_t s, uint64_t request);
 
 /* Counters and latency percentiles over the requests completed so far. */
 rmdec_status rmdec_server_stats_get(rmdec_server_t s, rmdec_server_stats *out);

@@ -16,7 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librmdec.so")
 
-OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEDOUT, EDEVICE = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEDOUT, EDEVICE, ECANCELED = 0, -1, -2, -3, -4, -5, -6, -7
 DTYPES = {"f32": 0, "i8": 1, "f16": 2, "i16": 3}
 PERM_REC = 11
 
@@ -67,6 +67,7 @@ def load_library():
         "rmdec_graph_create": ([V, V, I64, V, ctypes.POINTER(V)], I),
         "rmdec_graph_launch": ([V, V], I),
         "rmdec_graph_destroy": ([V], None),
+        "rmdec_debug_fail_device_allocs": ([I64], I),
         "rmdec_group_create": ([ctypes.POINTER(V), ctypes.POINTER(V), I], I),
         "rmdec_group_decode": ([V, ctypes.POINTER(_Segment), I, V], I),
         "rmdec_group_set_tuning": ([V, I, I], I),
@@ -301,6 +302,13 @@ class Group:
             pass
 
 
+def debug_fail_device_allocs(n):
+    """Test hook: the library's next n device allocations fail as if out of memory (0 disarms)."""
+    st = load_library().rmdec_debug_fail_device_allocs(int(n))
+    if st != OK:
+        raise RmdecError(st, "bad count")
+
+
 def unpack_bits(words, nbits):
     """[F, W] int32/uint32 words -> [F, nbits] uint8 (bit j = bit j%32 of word j//32)."""
     w = np.asarray(words).astype(np.uint32)
@@ -329,7 +337,8 @@ class _ServerStats(ctypes.Structure):
                 ("frames_completed", ctypes.c_int64), ("batches", ctypes.c_int64),
                 ("queued", ctypes.c_int64), ("in_flight", ctypes.c_int64),
                 ("latency_p50_us", ctypes.c_double), ("latency_p99_us", ctypes.c_double),
-                ("latency_max_us", ctypes.c_double), ("busy_seconds", ctypes.c_double)]
+                ("latency_max_us", ctypes.c_double), ("busy_seconds", ctypes.c_double),
+                ("cancelled", ctypes.c_int64)]
 
 
 def _load_server_api(lib):
@@ -342,6 +351,7 @@ def _load_server_api(lib):
         "rmdec_server_submit": ([V, I, V, I64, V, ctypes.POINTER(U64)], I),
         "rmdec_server_poll": ([V, U64, I64, ctypes.POINTER(D)], I),
         "rmdec_server_stats_get": ([V, ctypes.POINTER(_ServerStats)], I),
+        "rmdec_server_cancel": ([V, U64], I),
         "rmdec_server_destroy": ([V], None),
         "rmdec_server_last_error": ([V], ctypes.c_char_p),
     }
@@ -386,12 +396,20 @@ class Server:
         return rid.value
 
     def poll(self, request, timeout_us=0):
-        """Returns (status, latency_us); status OK, EBUSY or ETIMEDOUT (others raise)."""
+        """Returns (status, latency_us); status OK, EBUSY, ETIMEDOUT or ECANCELED (others raise)."""
         lat = ctypes.c_double(-1.0)
         st = self._lib.rmdec_server_poll(self._h, request, int(timeout_us), ctypes.byref(lat))
-        if st in (OK, EBUSY, ETIMEDOUT):
+        if st in (OK, EBUSY, ETIMEDOUT, ECANCELED):
             return st, lat.value
         self._check(st)
+
+    def cancel(self, request):
+        """Cancels a request not yet admitted: returns True, or False if it was already admitted."""
+        st = self._lib.rmdec_server_cancel(self._h, request)
+        if st == EBUSY:
+            return False
+        self._check(st)
+        return True
 
     def stats(self):
         s = _ServerStats()

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/rmdec.h"
 #include "../../include/rmdec_group.h"
@@ -136,8 +137,10 @@ rmdec_status launch_grouped(rmdec_group* g, const rmdec_segment* segs, std::vect
         a.total = total;
         const unsigned grid = (unsigned)std::min<int64_t>(total, (int64_t)g->sm_count * per_sm);
         void* args[] = {&a};
-        if ((e = cudaLaunchKernel(g->fn, dim3(grid), dim3(32 * W), args, smem_for(W), st)) != cudaSuccess)
-            return g->fail(RMDEC_ECUDA, "group kernel launch: %s", cudaGetErrorString(e));
+        nvtxRangePushA("rmdec_group_decode");
+        e = cudaLaunchKernel(g->fn, dim3(grid), dim3(32 * W), args, smem_for(W), st);
+        nvtxRangePop();
+        if (e != cudaSuccess) return g->fail(RMDEC_ECUDA, "group kernel launch: %s", cudaGetErrorString(e));
     }
     return RMDEC_OK;
 }

@@ -1,5 +1,6 @@
 // C-ABI of the rmdec library: handle management, permutation tables, kernel dispatch and
 // the asynchronous ticket interface. See include/rmdec.h for the contract of each call.
+#include <atomic>
 #include <cerrno>
 #include <chrono>
 #include <cstdarg>
@@ -15,6 +16,7 @@
 
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/rmdec.h"
 #include "pfht_kernel.cuh"
@@ -114,6 +116,7 @@ void compose(const uint16_t* outer, const uint16_t* inner, int s, uint16_t* out)
 int n_perm_levels(int m, int r) { return (1 < r && r < m - 1) ? r - 1 : 0; }
 
 thread_local std::string g_create_error;
+std::atomic<int64_t> g_failing_allocs{0};  // device allocations still to fail (test hook)
 
 }  // namespace
 
@@ -222,8 +225,8 @@ rmdec_status ensure_device(rmdec_ctx* h) {
     if (h->d_info) cudaFree(h->d_info);
     h->d_recs = nullptr;
     h->d_info = nullptr;
-    if ((e = cudaMalloc(&h->d_recs, std::max<size_t>(recs.size(), 1) * 2)) != cudaSuccess) return h->fail(RMDEC_ENOMEM, "cudaMalloc records: %s", cudaGetErrorString(e));
-    if ((e = cudaMalloc(&h->d_info, std::max<size_t>(h->info.size(), 1) * 2)) != cudaSuccess) return h->fail(RMDEC_ENOMEM, "cudaMalloc info: %s", cudaGetErrorString(e));
+    if ((e = rmdec_host::device_alloc(reinterpret_cast<void**>(&h->d_recs), std::max<size_t>(recs.size(), 1) * 2)) != cudaSuccess) return h->fail(RMDEC_ENOMEM, "cudaMalloc records: %s", cudaGetErrorString(e));
+    if ((e = rmdec_host::device_alloc(reinterpret_cast<void**>(&h->d_info), std::max<size_t>(h->info.size(), 1) * 2)) != cudaSuccess) return h->fail(RMDEC_ENOMEM, "cudaMalloc info: %s", cudaGetErrorString(e));
     std::vector<uint16_t> info16(h->info.begin(), h->info.end());
     if ((e = cudaMemcpy(h->d_recs, recs.data(), recs.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess) return h->cuda_fail(e, "upload records");
     if ((e = cudaMemcpy(h->d_info, info16.data(), info16.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess) return h->cuda_fail(e, "upload info");
@@ -318,7 +321,9 @@ rmdec_status launch(rmdec_ctx* h, const void* llr, int64_t n_frames, uint32_t* b
     const int64_t cap = (int64_t)h->sm_count * h->blocks_per_sm;
     const unsigned grid = (unsigned)std::min<int64_t>(n_frames, cap);
     void* args[] = {&a};
+    nvtxRangePushA(h->algo == 0 ? "rmdec_decode pfht" : "rmdec_decode aut-ssc");
     cudaError_t e = cudaLaunchKernel(h->kern.fn, dim3(grid), dim3(32 * h->warps), args, h->smem, stream);
+    nvtxRangePop();
     if (e != cudaSuccess) return h->cuda_fail(e, "kernel launch");
     return RMDEC_OK;
 }
@@ -371,6 +376,13 @@ rmdec_status make_handle(rmdec_t* out, int algo, int m, int r, int P, int L, uin
 
 namespace rmdec_host {
 size_t llr_elem_bytes_of(rmdec_ctx* h) { return llr_elem_bytes(h->dtype); }
+
+cudaError_t device_alloc(void** p, size_t bytes) {
+    int64_t n = g_failing_allocs.load();
+    while (n > 0)
+        if (g_failing_allocs.compare_exchange_weak(n, n - 1)) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
 
 rmdec_status member_info(rmdec_ctx* h, bool prepare, MemberInfo* out) {
     if (!h || !out) return RMDEC_EINVAL;
@@ -502,7 +514,7 @@ rmdec_status rmdec_decode_host(rmdec_t h, const void* llr_host, int64_t n_frames
             h->d_stage = nullptr;
             h->stage_bytes = 0;
         }
-        if ((e = cudaMalloc(&h->d_stage, in_pad + out_bytes)) != cudaSuccess)
+        if ((e = rmdec_host::device_alloc(&h->d_stage, in_pad + out_bytes)) != cudaSuccess)
             return h->fail(RMDEC_ENOMEM, "staging allocation of %zu bytes: %s", in_pad + out_bytes, cudaGetErrorString(e));
         h->stage_bytes = in_pad + out_bytes;
     }
@@ -630,7 +642,7 @@ rmdec_status rmdec_autotune(rmdec_t h, int64_t n_frames, const char* cache_path,
         }
     }
     void* d = nullptr;
-    cudaError_t e = cudaMalloc(&d, in_b + out_b + 256);
+    cudaError_t e = rmdec_host::device_alloc(&d, in_b + out_b + 256);
     if (e != cudaSuccess) return h->fail(RMDEC_ENOMEM, "autotune buffers: %s", cudaGetErrorString(e));
     cudaStream_t s = (cudaStream_t)stream;
     uint8_t* din = static_cast<uint8_t*>(d);
@@ -701,7 +713,7 @@ rmdec_status rmdec_graph_create(rmdec_t h, const void* llr_host, int64_t n_frame
     g->h = h;
     const size_t in_b = (size_t)n_frames * h->n * llr_elem_bytes(h->dtype), in_pad = (in_b + 255) / 256 * 256;
     const size_t out_b = (size_t)n_frames * ((h->k + 31) / 32) * 4;
-    cudaError_t e = cudaMalloc(&g->dbuf, in_pad + out_b);
+    cudaError_t e = rmdec_host::device_alloc(&g->dbuf, in_pad + out_b);
     if (e != cudaSuccess) {
         delete g;
         return h->fail(RMDEC_ENOMEM, "graph buffers: %s", cudaGetErrorString(e));
@@ -742,6 +754,12 @@ void rmdec_graph_destroy(rmdec_graph_t g) {
     cudaGraphDestroy(g->graph);
     cudaFree(g->dbuf);
     delete g;
+}
+
+rmdec_status rmdec_debug_fail_device_allocs(int64_t n) {
+    if (n < 0) return RMDEC_EINVAL;
+    g_failing_allocs.store(n);
+    return RMDEC_OK;
 }
 
 const char* rmdec_last_error(rmdec_t h) {

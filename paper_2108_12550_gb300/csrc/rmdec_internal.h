@@ -12,6 +12,10 @@ struct rmdec_ctx;
 
 namespace rmdec_host {
 
+// Every device allocation of the library goes through here, so that tests can make it fail
+// (rmdec_debug_fail_device_allocs).
+cudaError_t device_alloc(void** p, size_t bytes);
+
 // Bytes per LLR element of a handle's current input type.
 size_t llr_elem_bytes_of(rmdec_ctx* h);
 

@@ -29,6 +29,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/rmdec.h"
 #include "../../include/rmdec_group.h"
@@ -135,7 +136,7 @@ struct rmdec_server {
     std::thread worker;
     bool stop = false;
     uint64_t next_id = 1;
-    int64_t n_submitted = 0, n_completed = 0, frames_completed = 0, n_batches = 0;
+    int64_t n_submitted = 0, n_completed = 0, frames_completed = 0, n_batches = 0, n_cancelled = 0;
     std::vector<double> latencies;
     bool have_first = false;
     Clock::time_point t_first, t_last;
@@ -262,6 +263,7 @@ struct rmdec_server {
         rmdec_group_t grp = fused ? families[fam].grp : nullptr;
         lk.unlock();
         cudaStream_t st = streams[sidx];
+        nvtxRangePushA(grp ? "rmdec_server_batch_fused" : "rmdec_server_batch");
         uint8_t* base = static_cast<uint8_t*>(arena_ptr) + off;
         bool ok = true;
         std::vector<int64_t> at(parts.size(), 0);  // frames placed so far per part
@@ -297,6 +299,7 @@ struct rmdec_server {
         }
         cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
         cudaEventRecord(b->ev, st);
+        nvtxRangePop();
         b->failed = !ok;
         lk.lock();
         inflight.push_back(b);
@@ -344,7 +347,7 @@ rmdec_status rmdec_server_create(rmdec_server_t* out, const rmdec_server_config*
         delete s;
         return RMDEC_EDEVICE;
     }
-    if ((e = cudaMalloc(&s->arena_ptr, (size_t)cfg->arena_bytes)) != cudaSuccess) {
+    if ((e = rmdec_host::device_alloc(&s->arena_ptr, (size_t)cfg->arena_bytes)) != cudaSuccess) {
         g_server_error = std::string("arena allocation: ") + cudaGetErrorString(e);
         delete s;
         return RMDEC_ENOMEM;
@@ -429,6 +432,24 @@ rmdec_status rmdec_server_poll(rmdec_server_t s, uint64_t request, int64_t timeo
     return st;
 }
 
+rmdec_status rmdec_server_cancel(rmdec_server_t s, uint64_t request) {
+    if (!s) return RMDEC_EINVAL;
+    std::lock_guard<std::mutex> g(s->mu);
+    auto it = s->requests.find(request);
+    if (it == s->requests.end()) return s->fail(RMDEC_EINVAL, "unknown request %llu", (unsigned long long)request);
+    Request* r = it->second;
+    auto pit = std::find(s->pending.begin(), s->pending.end(), r);
+    if (pit == s->pending.end())
+        return s->fail(RMDEC_EBUSY, "request %llu was already admitted", (unsigned long long)request);
+    s->pending.erase(pit);
+    r->done = true;
+    r->status = RMDEC_ECANCELED;
+    r->t_done = Clock::now();
+    s->n_cancelled++;
+    s->cv_done.notify_all();
+    return RMDEC_OK;
+}
+
 rmdec_status rmdec_server_stats_get(rmdec_server_t s, rmdec_server_stats* out) {
     if (!s || !out) return RMDEC_EINVAL;
     std::lock_guard<std::mutex> g(s->mu);
@@ -438,6 +459,7 @@ rmdec_status rmdec_server_stats_get(rmdec_server_t s, rmdec_server_stats* out) {
     out->frames_completed = s->frames_completed;
     out->batches = s->n_batches;
     out->queued = (int64_t)s->pending.size();
+    out->cancelled = s->n_cancelled;
     int64_t inf = 0;
     for (Batch* b : s->inflight) inf += (int64_t)b->reqs.size();
     out->in_flight = inf;
