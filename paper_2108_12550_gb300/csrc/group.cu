@@ -113,7 +113,7 @@ rmdec_status launch_grouped(rmdec_group* g, const rmdec_segment* segs, std::vect
         gd.cfg = group_cfg_index(mi[d].m, mi[d].r);
         gd.P = mi[d].P;
         gd.K = mi[d].k;
-        gd.rec_elems = mi[d].P * mi[d].nrec * kRec;
+        gd.rec_elems = mi[d].nrec * kRec;
         gd.dtype = mi[d].dtype;
         gd.qclamp = (float)((1 << (24 - mi[d].m)) - 1);
         gd.single = mi[d].single;

@@ -27,11 +27,11 @@ constexpr int kGroupMaxSeg = 224;  // segments per launch (the host splits longe
 __host__ __device__ constexpr int group_cfg_index(int m, int r) { return (m - 4) * 2 + (r - 2); }
 
 struct GroupDec {
-    const uint16_t* recs;  // device records, P * NREC * kRec
+    const uint16_t* recs;  // device table: per decoder NREC maps, then their inverses
     const uint16_t* info;  // K information positions
     int cfg;               // group_cfg_index(m, r)
     int P, K;
-    int rec_elems;         // P * NREC * kRec
+    int rec_elems;         // NREC * kRec: forward map elements per decoder
     int dtype;
     float qclamp;
     int single;
@@ -85,11 +85,12 @@ __global__ void __launch_bounds__(128, 5) group_kernel(const __grid_constant__ G
         const GroupDec& d = a.dec[sg.dec];
         if (sg.dec != loaded) {
             __syncthreads();  // every warp is done with the previous decoder's tables
-            for (int i = threadIdx.x; i < d.rec_elems; i += blockDim.x) sm.rec[i] = d.recs[i];
+            copy_maps(sm.rec, d.recs, d.P, d.rec_elems);
             for (int i = threadIdx.x; i < d.K; i += blockDim.x) sm.info[i] = d.info[i];
             loaded = sg.dec;  // decode_frame's first barrier publishes the tables
         }
         FrameJob j;
+        j.recs = d.recs;
         j.llr = sg.llr;
         j.dtype = d.dtype;
         j.qclamp = d.qclamp;

@@ -41,7 +41,7 @@ struct LaunchArgs {
     float qclamp;  // |code| clamp for I16 inputs
     int64_t n_frames;
     int P;
-    const uint16_t* recs;  // device records, P * NREC * kRec
+    const uint16_t* recs;  // device records: per decoder NREC maps, then their NREC inverses
     const uint16_t* info;  // K information positions
     int K;
     uint32_t* info_out;  // [F][ceil(K/32)]
@@ -57,7 +57,8 @@ struct Cfg {
     static constexpr int N = 1 << M;
     static constexpr int NW = N >= 32 ? N / 32 : 1;
     static constexpr int NLEV = R - 1;           // permuted nodes: levels M, M-1, ..., M-R+2
-    static constexpr int NREC = 2 * L * NLEV;    // device records per decoder
+    static constexpr int NREC = 2 * L * NLEV;    // candidate permutations per decoder (device
+                                                 // tables: NREC maps, then their NREC inverses)
     static constexpr int MIN_DEEP = M - R + 2;   // lowest permuted level
 
     static __host__ __device__ constexpr int lanes(int s) { return cmin(32 / L, 1 << s); }
@@ -95,7 +96,8 @@ struct Warp {
     uint32_t* best;     // NW: this warp's best codeword so far
     uint8_t* spc;       // L x 32 SPC order scratch
     const float* y;     // frame LLRs
-    const uint16_t* rec;  // this decoder's NREC records
+    const uint16_t* rec;      // this decoder's NREC records (shared memory)
+    const uint16_t* rec_inv;  // their inverse maps (global memory; read only to un-permute)
     int lane;
     int bsel;           // current bit buffer (warp uniform)
     bool single;        // paths 1..L-1 start inactive (metric +inf)
@@ -709,22 +711,25 @@ struct Decoder {
                     constexpr int SB = 1 << S;
                     if constexpr (SB >= 32) {
                         constexpr int SW = SB / 32;
+                        // gather form x[j] = x'[pi^-1(j)]: word t of the result is the
+                        // ballot of lane j's source bits; lane t keeps it until every lane
+                        // has read the path's old bits
+                        static_assert(SW <= 32, "one result word per lane");
 #pragma unroll 1
                         for (int l = 0; l < L; l++) {
                             const int cl = __shfl_sync(kFull, ps.selc[S], l);
-                            const uint16_t* r = lrec + cl * kRec;
+                            const uint16_t* ri = w.rec_inv + (LEVEL * 2 * L + cl) * kRec;
                             uint32_t* b = bitbuf(w, w.bsel, l);
-                            for (int wd = w.lane; wd < SW; wd += 32) w.xtmp[wd] = 0;
-                            __syncwarp();
-                            const int base = ga_lane_base(r, S, w.lane);
+                            const int base = ga_lane_base(ri, S, w.lane);
+                            unsigned mine = 0;
 #pragma unroll
                             for (int t = 0; t < SW; t++) {
-                                const int dstp = base ^ ga_hi(r, S, t);
-                                const unsigned bit = (b[t] >> w.lane) & 1u;
-                                if (bit) atomicOr(&w.xtmp[dstp >> 5], 1u << (dstp & 31));
+                                const int srcp = base ^ ga_hi(ri, S, t);
+                                const unsigned word = __ballot_sync(kFull, (b[srcp >> 5] >> (srcp & 31)) & 1u);
+                                if (w.lane == t) mine = word;
                             }
                             __syncwarp();
-                            for (int wd = w.lane; wd < SW; wd += 32) b[wd] = w.xtmp[wd];
+                            if (w.lane < SW) b[w.lane] = mine;
                             __syncwarp();
                         }
                     } else {
@@ -766,7 +771,8 @@ struct Decoder {
 
     // Root combine and un-permutation of path 0 into `dst` (the codeword in the channel
     // domain): x_root = (x_gamma ^ x_lambda, x_gamma), then x[sigma(i)] = x'[i] with
-    // sigma = pi^init o pi* the path's composed root permutation (Algorithm 2, lines 17-21).
+    // sigma = pi^init o pi* the path's composed root permutation (Algorithm 2, lines 17-21),
+    // read through the inverse map the host stores after the decoder's records.
     __device__ static void emit(Warp& w, int c0, uint32_t* dst) {
         uint32_t* b = bitbuf(w, w.bsel, 0);
         constexpr int H = N / 2;
@@ -775,18 +781,21 @@ struct Decoder {
         } else if (w.lane == 0) {
             b[0] ^= (b[0] >> H) & ((1u << H) - 1u);
         }
-        for (int wd = w.lane; wd < NW; wd += 32) dst[wd] = 0;
         __syncwarp();
-        const uint16_t* r = w.rec + c0 * kRec;
-        const int base = ga_lane_base(r, M, w.lane);
+        // gather form x[j] = x'[sigma^-1(j)]: word t of the codeword is the ballot of lane j's
+        // source bits
+        static_assert(NW <= 32, "one codeword word per lane");
+        const uint16_t* ri = w.rec_inv + c0 * kRec;
+        const int base = ga_lane_base(ri, M, w.lane);
+        unsigned mine = 0;
 #pragma unroll
-        for (int t = 0; t < (N + 31) / 32; t++) {
-            const int i = w.lane + 32 * t;
-            if (i < N) {
-                const int dstp = base ^ ga_hi(r, M, t);
-                if ((b[i >> 5] >> (i & 31)) & 1u) atomicOr(&dst[dstp >> 5], 1u << (dstp & 31));
-            }
+        for (int t = 0; t < NW; t++) {
+            const int srcp = base ^ ga_hi(ri, M, t);
+            const bool in = w.lane + 32 * t < N;
+            const unsigned word = __ballot_sync(kFull, in && ((b[srcp >> 5] >> (srcp & 31)) & 1u));
+            if (w.lane == t) mine = word;
         }
+        if (w.lane < NW) dst[w.lane] = mine;
         __syncwarp();
     }
 };
@@ -801,6 +810,12 @@ __host__ __device__ constexpr int frame_fixed_bytes(int rec_elems, int K, int N,
 template <int M, int R, int L>
 __host__ constexpr int Cfg<M, R, L>::fixed_bytes(int P, int K, int W) {
     return frame_fixed_bytes(P * NREC * kRec, K, N, W);
+}
+
+// The forward maps of P decoders (per decoder `per` elements, followed in the device table by
+// as many of inverse maps) into shared memory, whole block.
+__device__ __forceinline__ void copy_maps(uint16_t* dst, const uint16_t* recs, int P, int per) {
+    for (int i = threadIdx.x; i < P * per; i += blockDim.x) dst[i] = recs[(i / per) * 2 * per + i % per];
 }
 
 struct FrameSmem {
@@ -821,6 +836,7 @@ __device__ __forceinline__ FrameSmem carve_smem(uint8_t* smem, int rec_elems, in
 
 // What the decode of one frame reads and writes (output pointers may be null except info_out).
 struct FrameJob {
+    const uint16_t* recs;  // the decoders' device tables (maps, then inverse maps, per decoder)
     const void* llr;     // [frames][N] of dtype
     int dtype;
     float qclamp;        // |code| clamp for I16 inputs
@@ -881,6 +897,7 @@ __device__ __forceinline__ void decode_frame(const FrameJob& j, const FrameSmem&
     int bestp = -1;
     for (int p = warp; p < j.P; p += W) {
         w.rec = sm.rec + p * C::NREC * kRec;
+        w.rec_inv = j.recs + (2 * p + 1) * C::NREC * kRec;
         int c0;
         const float pm = D::run(w, c0);
         if (bestp < 0 || pm < best) {  // strict: earlier decoders win ties (Algorithm 5)
@@ -954,9 +971,10 @@ __global__ void __launch_bounds__(32 * kMaxWarps, 1) pfht_kernel(LaunchArgs args
     extern __shared__ __align__(16) uint8_t smem[];
     const int rec_elems = args.P * C::NREC * kRec;
     const FrameSmem sm = carve_smem(smem, rec_elems, args.K, C::WARP_BYTES);
-    for (int i = threadIdx.x; i < rec_elems; i += blockDim.x) sm.rec[i] = args.recs[i];
+    copy_maps(sm.rec, args.recs, args.P, C::NREC * kRec);
     for (int i = threadIdx.x; i < args.K; i += blockDim.x) sm.info[i] = args.info[i];
     FrameJob j;
+    j.recs = args.recs;
     j.llr = args.llr;
     j.dtype = args.dtype;
     j.qclamp = args.qclamp;

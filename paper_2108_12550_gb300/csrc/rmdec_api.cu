@@ -113,6 +113,31 @@ void compose(const uint16_t* outer, const uint16_t* inner, int s, uint16_t* out)
     out[kMaxM] = (uint16_t)(lin(inner[kMaxM]) ^ outer[kMaxM]);
 }
 
+// Inverse of the invertible affine map x -> A x ^ b of GF(2)^s as a record:
+// x -> A^-1 x ^ A^-1 b (Gauss-Jordan elimination on the rows of [A | I]).
+void invert(const uint16_t* r, int s, uint16_t* out) {
+    uint32_t row[kMaxM];
+    for (int i = 0; i < s; i++) {
+        uint32_t a = 0;
+        for (int t = 0; t < s; t++) a |= (uint32_t)((r[t] >> i) & 1u) << t;  // A[i][t] = bit i of column t
+        row[i] = a | (1u << (s + i));
+    }
+    for (int col = 0; col < s; col++) {
+        int piv = col;
+        while (!((row[piv] >> col) & 1u)) piv++;  // exists: A is invertible
+        std::swap(row[col], row[piv]);
+        for (int i = 0; i < s; i++)
+            if (i != col && ((row[i] >> col) & 1u)) row[i] ^= row[col];
+    }
+    memset(out, 0, sizeof(uint16_t) * kRec);
+    for (int t = 0; t < s; t++)
+        for (int i = 0; i < s; i++) out[t] |= (uint16_t)(((row[i] >> (s + t)) & 1u) << i);
+    uint16_t v = 0;
+    for (int t = 0; t < s; t++)
+        if ((r[kMaxM] >> t) & 1u) v ^= out[t];
+    out[kMaxM] = v;
+}
+
 int n_perm_levels(int m, int r) { return (1 < r && r < m - 1) ? r - 1 : 0; }
 
 thread_local std::string g_create_error;
@@ -192,21 +217,26 @@ bool lookup_kernel(rmdec_ctx* h, rmdec_host::KernelEntry* e) {
 
 // Device records: p-FHT-FSCL: per decoder, level 0 holds the 2L root candidates composed with
 // the initial permutation of their source path (pi^init_{c mod L} o pi_c, one GA(m) element, since
-// every root path starts from the same channel LLRs), levels 1.. hold the 2L candidates as given.
+// every root path starts from the same channel LLRs), levels 1.. hold the 2L candidates as given;
+// then the inverse of each of these maps in the same order (the kernel un-permutes decided
+// words by gathering through them).
 std::vector<uint16_t> device_records(const rmdec_ctx* h) {
     std::vector<uint16_t> out;
     if (h->algo == 1) return h->perms;
     const int rpd = h->records_per_decoder(), nlev = n_perm_levels(h->m, h->r), L = h->L;
-    out.resize((size_t)h->P * nlev * 2 * L * kRec);
+    const size_t nrec = (size_t)nlev * 2 * L;  // maps per decoder
+    out.resize((size_t)h->P * 2 * nrec * kRec);
     for (int p = 0; p < h->P; p++) {
         const uint16_t* base = h->perms.data() + (size_t)p * rpd * kRec;
-        uint16_t* dst = out.data() + (size_t)p * nlev * 2 * L * kRec;
+        uint16_t* dst = out.data() + (size_t)p * 2 * nrec * kRec;
         for (int lev = 0; lev < nlev; lev++)
             for (int c = 0; c < 2 * L; c++) {
                 const uint16_t* cand = base + (size_t)(L + lev * 2 * L + c) * kRec;
-                uint16_t* o = dst + (size_t)(lev * 2 * L + c) * kRec;
+                const size_t q = (size_t)lev * 2 * L + c;
+                uint16_t* o = dst + q * kRec;
                 if (lev == 0) compose(base + (size_t)(c % L) * kRec, cand, h->m, o);
                 else memcpy(o, cand, sizeof(uint16_t) * kRec);
+                invert(o, h->m - lev, dst + (nrec + q) * kRec);
             }
     }
     return out;

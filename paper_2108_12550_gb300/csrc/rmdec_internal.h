@@ -23,7 +23,7 @@ size_t llr_elem_bytes_of(rmdec_ctx* h);
 struct KernelEntry {
     const void* fn = nullptr;  // __global__ function
     int warp_bytes = 0;        // shared memory per warp
-    int nrec = 0;              // device permutation records per decoder
+    int nrec = 0;              // permutation maps per decoder (the device table adds their inverses)
     int (*fixed_bytes)(int P, int K, int W) = nullptr;
 };
 
