@@ -55,20 +55,21 @@ struct GroupArgs {
     int64_t total;         // frames over all segments
 };
 
+// Members' P need not be multiples of the block's warps, so no leaf barriers here (LOCK false).
 template <int L>
 __device__ __forceinline__ void group_dispatch(int cfg, const FrameJob& j, const FrameSmem& sm, int64_t f) {
     switch (cfg) {
-        case group_cfg_index(4, 2): decode_frame<4, 2, L>(j, sm, f); break;
-        case group_cfg_index(5, 2): decode_frame<5, 2, L>(j, sm, f); break;
-        case group_cfg_index(5, 3): decode_frame<5, 3, L>(j, sm, f); break;
-        case group_cfg_index(6, 2): decode_frame<6, 2, L>(j, sm, f); break;
-        case group_cfg_index(6, 3): decode_frame<6, 3, L>(j, sm, f); break;
-        case group_cfg_index(7, 2): decode_frame<7, 2, L>(j, sm, f); break;
-        case group_cfg_index(7, 3): decode_frame<7, 3, L>(j, sm, f); break;
-        case group_cfg_index(8, 2): decode_frame<8, 2, L>(j, sm, f); break;
-        case group_cfg_index(8, 3): decode_frame<8, 3, L>(j, sm, f); break;
-        case group_cfg_index(9, 2): decode_frame<9, 2, L>(j, sm, f); break;
-        case group_cfg_index(9, 3): decode_frame<9, 3, L>(j, sm, f); break;
+        case group_cfg_index(4, 2): decode_frame<4, 2, L, false>(j, sm, f); break;
+        case group_cfg_index(5, 2): decode_frame<5, 2, L, false>(j, sm, f); break;
+        case group_cfg_index(5, 3): decode_frame<5, 3, L, false>(j, sm, f); break;
+        case group_cfg_index(6, 2): decode_frame<6, 2, L, false>(j, sm, f); break;
+        case group_cfg_index(6, 3): decode_frame<6, 3, L, false>(j, sm, f); break;
+        case group_cfg_index(7, 2): decode_frame<7, 2, L, false>(j, sm, f); break;
+        case group_cfg_index(7, 3): decode_frame<7, 3, L, false>(j, sm, f); break;
+        case group_cfg_index(8, 2): decode_frame<8, 2, L, false>(j, sm, f); break;
+        case group_cfg_index(8, 3): decode_frame<8, 3, L, false>(j, sm, f); break;
+        case group_cfg_index(9, 2): decode_frame<9, 2, L, false>(j, sm, f); break;
+        case group_cfg_index(9, 3): decode_frame<9, 3, L, false>(j, sm, f); break;
         default: break;  // rejected on the host
     }
 }

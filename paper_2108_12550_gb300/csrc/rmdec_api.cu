@@ -293,18 +293,17 @@ rmdec_status configure_shape(rmdec_ctx* h) {
         if (const char* s = getenv("RMDEC_WARPS")) W = atoi(s);
     if (!W) {
         // default: the most resident warps per SM; among equals, warps that split the P
-        // decoders evenly, then at least two decoders per warp and at least two CTAs per SM
-        // (a lone decoder per warp, or a lone CTA, leaves the SM idle at every frame
-        // boundary). Last, the CTA width: the m = 9 trees compile to 80-380 KB of straight-line
-        // code, more than the instruction caches hold, and run fastest in the widest CTA,
-        // whose warps walk the tree's code together; smaller codes fit and run fastest in
-        // the narrowest CTAs, which never wait for each other.
-        const bool wide = h->m >= 9;
+        // decoders evenly (which also lets the kernel align its warps at every leaf), then at
+        // least two decoders per warp and at least two CTAs per SM (a lone decoder per warp,
+        // or a lone CTA, leaves the SM idle at every frame boundary), then the narrowest CTA:
+        // more CTAs per SM hide each other's barrier waits, while the leaf barriers keep the
+        // warps of one CTA on the same code (measured on RM(2,9) P=20 L=4: 4 warps x 5 CTAs
+        // 5.73 M frames/s, 5 x 4 5.57 M, 10 x 2 5.45 M, 20 x 1 5.16 M)
         auto score = [&](int c) {
             const int occ = occ_for(c);
             const bool even = h->algo != 0 || h->P % c == 0;
             const bool two_each = h->algo != 0 || h->P >= 2 * c;
-            return std::make_tuple(occ * c, even, two_each, occ >= 2, wide ? c : -c);
+            return std::make_tuple(occ * c, even, two_each, occ >= 2, -c);
         };
         auto best = score(1);
         W = 1;
