@@ -447,26 +447,40 @@ struct Decoder {
             }
         }
         __syncwarp();
+        // Lane l < L keeps, for path l as SPC-entry ancestor, its LRB and, in split order, the
+        // next TAU positions and reliabilities; every round takes the values of each path's
+        // ancestor with shuffles, and the lanes then shift their own lists by one.
         const int me = w.lane < L ? w.lane : 0;
+        const float* am = buf + me * ST;
+        const int o0 = w.spc[me * 32];
+        const float lrb = fabsf(am[o0]);
+        float rel[TAU];
+        int pos[TAU];
+#pragma unroll
+        for (int t = 0; t < TAU; t++) {
+            pos[t] = w.spc[me * 32 + 1 + t];
+            rel[t] = fabsf(am[pos[t]]);
+        }
         float pm;
         int p;
         {
-            const float* am = buf + me * ST;
             unsigned hd0 = 0;
 #pragma unroll
             for (int i = 0; i < NS; i++) hd0 |= (am[i] < 0.f ? 1u : 0u) << i;
             p = __popc(hd0) & 1;
-            pm = ps.pm + (p ? fabsf(am[w.spc[me * 32]]) : 0.f);  // Eq. (3)
+            pm = ps.pm + (p ? lrb : 0.f);  // Eq. (3)
         }
+        __syncwarp();  // the order lists are read; w.spc now holds the selection of each round
+        uint8_t* sel = w.spc;
         unsigned flip = 0;
         int orig = me;
 #pragma unroll 1
         for (int t = 1; t <= TAU; t++) {
             // the split position and the LRB belong to the path's SPC-entry ancestor `orig`
-            const float* ao = buf + orig * ST;
-            const int itp = w.spc[orig * 32 + t];
-            const float lrb = fabsf(ao[w.spc[orig * 32]]);
-            const float pflip = pm + fabsf(ao[itp]) + (p ? -lrb : lrb);  // Eq. (4)
+            const float r_o = __shfl_sync(kFull, rel[0], orig);
+            const int itp = __shfl_sync(kFull, pos[0], orig);
+            const float lrb_o = __shfl_sync(kFull, lrb, orig);
+            const float pflip = pm + r_o + (p ? -lrb_o : lrb_o);  // Eq. (4)
             const int src = w.lane < 2 * L ? (w.lane >> 1) : 0;
             const float kpm = __shfl_sync(kFull, pm, src);
             const float fpm = __shfl_sync(kFull, pflip, src);
@@ -478,12 +492,11 @@ struct Decoder {
                 const float o = __shfl_sync(kFull, cpm, c2);
                 rank += (o < cpm) || (o == cpm && c2 < w.lane);
             }
-            int mysrc = 0;
-#pragma unroll
-            for (int q = 0; q < L; q++) {
-                const unsigned b = __ballot_sync(kFull, w.lane < 2 * L && rank == q);
-                if (w.lane == q) mysrc = __ffs(b) - 1;
-            }
+            // candidate of rank q goes to path q
+            if (w.lane < 2 * L && rank < L) sel[rank] = (uint8_t)w.lane;
+            __syncwarp();
+            const int mysrc = sel[me];
+            __syncwarp();
             const int sp = mysrc >> 1;
             const bool fl = mysrc & 1;
             // state of the source path: metric, ancestor, flips, parity, split position
@@ -497,6 +510,11 @@ struct Decoder {
             const int n_it = (int)(packed >> 16);
             flip = fl ? (n_flip ^ (1u << n_it)) : n_flip;  // Eq. (5)
             p = fl ? (int)(((packed >> 8) & 1u) ^ 1u) : (int)((packed >> 8) & 1u);
+#pragma unroll
+            for (int k = 0; k + 1 < TAU; k++) {
+                rel[k] = rel[k + 1];
+                pos[k] = pos[k + 1];
+            }
         }
         unsigned x;
         {
@@ -504,9 +522,9 @@ struct Decoder {
             unsigned hd = 0;
 #pragma unroll
             for (int i = 0; i < NS; i++) hd |= (ao[i] < 0.f ? 1u : 0u) << i;
-            const int o0 = w.spc[orig * 32];
-            x = (hd ^ flip) & ~(1u << o0);
-            x |= (unsigned)(__popc(x) & 1) << o0;  // Eq. (6)
+            const int lo0 = __shfl_sync(kFull, o0, orig);
+            x = (hd ^ flip) & ~(1u << lo0);
+            x |= (unsigned)(__popc(x) & 1) << lo0;  // Eq. (6)
         }
         reselect<OFF, PEND>(w, ps, orig, pm);
         put_small_bits<OFF, NS>(w, x);
