@@ -134,7 +134,9 @@ rmdec_status rmdec_poll(rmdec_t h, uint64_t ticket, int64_t timeout_us);
  * of a frame are split across a CTA's warps) and a cap on resident CTAs per SM (0 = the
  * occupancy limit); 0 warps = the default: the most resident warps per SM, then warps that
  * split the P decoders evenly, then two or more decoders per warp and two or more CTAs per
- * SM, then the widest CTA for m = 9 and the narrowest below (see rmdec_autotune). A shape
+ * SM, then the narrowest CTA; a launch of at most four waves of that shape takes the shape
+ * with the fewest waves x rounds of decoders per warp instead (wider CTAs run more of each
+ * frame's decoders at once; see also rmdec_autotune). A shape
  * whose shared memory does not fit fails the next decode with RMDEC_EINVAL. Takes effect on
  * the next decode. Not part of the paper's method: it only changes scheduling, never
  * results. */

@@ -163,6 +163,9 @@ struct rmdec_ctx {
     int sm_count = 0;
     int blocks_per_sm = 0;
     size_t smem = 0;
+    bool auto_shape = true;          // shape chosen by configure_shape's default rule
+    std::vector<int> occ_w;          // resident CTAs per SM for W = 1.. warps per CTA (0: not resident)
+    std::vector<size_t> smem_w;      // dynamic shared memory for W warps per CTA
     void* d_stage = nullptr;
     size_t stage_bytes = 0;
     std::map<uint64_t, cudaEvent_t> tickets;
@@ -288,9 +291,16 @@ rmdec_status configure_shape(rmdec_ctx* h) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, h->kern.fn, 32 * W, smem_for(W)) != cudaSuccess) return 0;
         return o;
     };
+    h->occ_w.assign(wmax + 1, 0);
+    h->smem_w.assign(wmax + 1, 0);
+    for (int c = 1; c <= wmax; c++) {
+        h->occ_w[c] = occ_for(c);
+        h->smem_w[c] = smem_for(c);
+    }
     int W = h->req_warps;
     if (!W)
         if (const char* s = getenv("RMDEC_WARPS")) W = atoi(s);
+    h->auto_shape = W == 0;
     if (!W) {
         // default: the most resident warps per SM; among equals, warps that split the P
         // decoders evenly (which also lets the kernel align its warps at every leaf), then at
@@ -333,6 +343,30 @@ rmdec_status launch(rmdec_ctx* h, const void* llr, int64_t n_frames, uint32_t* b
     rmdec_status st = ensure_device(h);
     if (st == RMDEC_OK) st = configure_shape(h);
     if (st != RMDEC_OK) return st;
+    // Launches of a few waves: the last, partial wave costs a whole frame's worth of decoder
+    // rounds (P / W decoders one after another per warp), so such launches take the shape
+    // that minimises waves x rounds (ties: the default shape). Larger launches keep the
+    // default, whose per-warp throughput is measured best.
+    int W = h->warps, per_sm = h->blocks_per_sm;
+    size_t smem = h->smem;
+    const int64_t cap0 = (int64_t)h->sm_count * h->blocks_per_sm;
+    if (h->auto_shape && !h->req_ctas && h->algo == 0 && n_frames <= 4 * cap0) {
+        auto cost = [&](int c) {
+            const int64_t cap = (int64_t)h->sm_count * h->occ_w[c];
+            return ((n_frames + cap - 1) / cap) * (int64_t)((h->P + c - 1) / c);
+        };
+        int64_t best = cost(W);
+        for (int c = 1; c < (int)h->occ_w.size(); c++) {
+            if (h->occ_w[c] <= 0 || c == h->warps) continue;
+            const int64_t v = cost(c);
+            if (v < best) {
+                best = v;
+                W = c;
+                per_sm = h->occ_w[c];
+                smem = h->smem_w[c];
+            }
+        }
+    }
     rmdec_dev::LaunchArgs a;
     a.llr = llr;
     a.dtype = (int)h->dtype;
@@ -347,11 +381,11 @@ rmdec_status launch(rmdec_ctx* h, const void* llr, int64_t n_frames, uint32_t* b
     a.pm_out = pm;
     a.best_out = best;
     a.single_start = h->single_start ? 1 : 0;
-    const int64_t cap = (int64_t)h->sm_count * h->blocks_per_sm;
+    const int64_t cap = (int64_t)h->sm_count * per_sm;
     const unsigned grid = (unsigned)std::min<int64_t>(n_frames, cap);
     void* args[] = {&a};
     nvtxRangePushA(h->algo == 0 ? "rmdec_decode pfht" : "rmdec_decode aut-ssc");
-    cudaError_t e = cudaLaunchKernel(h->kern.fn, dim3(grid), dim3(32 * h->warps), args, h->smem, stream);
+    cudaError_t e = cudaLaunchKernel(h->kern.fn, dim3(grid), dim3(32 * W), args, smem, stream);
     nvtxRangePop();
     if (e != cudaSuccess) return h->cuda_fail(e, "kernel launch");
     return RMDEC_OK;
