@@ -36,7 +36,7 @@ WORKLOADS = {
 METRIC = "frames/s RM(2,9) P=20 L=4 at FER~1e-4 Eb/N0"
 # DRAM bytes per frame from the ncu capture summarised in profiles/pfht_kernel_rm29_p20_l4.md,
 # valid only for the kernel source it was taken on (sha256 prefix of pfht_kernel.cuh)
-TRAFFIC = {"rm29_p20_l4": {"bytes_per_frame": 33650176 / 16384, "kernel_sha256": "46aeb7ed719899ab"}}
+TRAFFIC = {"rm29_p20_l4": {"bytes_per_frame": 33650688 / 16384, "kernel_sha256": "b0b6df226c1b11b8"}}
 SMS = 152
 LANES_PER_SM = 128
 
