@@ -13,6 +13,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import re
 import subprocess
 import sys
 import time
@@ -35,10 +36,21 @@ WORKLOADS = {
 }
 METRIC = "frames/s RM(2,9) P=20 L=4 at FER~1e-4 Eb/N0"
 # DRAM bytes per frame from the ncu capture summarised in profiles/pfht_kernel_rm29_p20_l4.md,
-# valid only for the kernel source it was taken on (sha256 prefix of pfht_kernel.cuh)
-TRAFFIC = {"rm29_p20_l4": {"bytes_per_frame": 33650688 / 16384, "kernel_sha256": "b0b6df226c1b11b8"}}
+# valid only for the kernel code it was taken on (kernel_fingerprint() prefix)
+TRAFFIC = {"rm29_p20_l4": {"bytes_per_frame": 33650688 / 16384, "kernel_code_sha256": "17fcb70412a1705f"}}
 SMS = 152
 LANES_PER_SM = 128
+
+
+def kernel_fingerprint():
+    """sha256 of the kernel source with comments and blank lines removed: a capture stays
+    valid across comment edits and goes stale on any code change."""
+    import hashlib
+
+    with open(os.path.join(ROOT, "paper_2108_12550_gb300", "csrc", "pfht_kernel.cuh")) as fh:
+        code = re.sub(r"//[^\n]*", "", fh.read())
+    code = "\n".join(line.strip() for line in code.splitlines() if line.strip())
+    return hashlib.sha256(code.encode()).hexdigest()
 
 
 def _peaks():
@@ -442,12 +454,8 @@ def main():
     achieved = ops * nf / (ms * 1e-3)
     traffic = None
     tr = TRAFFIC.get(args.workload)
-    if tr and args.dtype == "f32":
-        import hashlib
-
-        with open(os.path.join(ROOT, "paper_2108_12550_gb300", "csrc", "pfht_kernel.cuh"), "rb") as fh:
-            if hashlib.sha256(fh.read()).hexdigest().startswith(tr["kernel_sha256"]):
-                traffic = tr["bytes_per_frame"] * nf  # scaled from the captured case by frames
+    if tr and args.dtype == "f32" and kernel_fingerprint().startswith(tr["kernel_code_sha256"]):
+        traffic = tr["bytes_per_frame"] * nf  # scaled from the captured case by frames
     line = {
         "metric": METRIC if args.workload == "rm29_p20_l4" else f"frames/s {args.workload}",
         "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

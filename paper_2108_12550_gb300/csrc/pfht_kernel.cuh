@@ -6,13 +6,15 @@
 //
 // Execution model. A CTA owns one frame at a time (persistent loop over frames). Its W warps
 // share the frame's LLRs in shared memory and split the P decoders round-robin; a warp runs
-// one decoder with all L list paths at once. The decoding tree is expanded at compile time
+// one decoder with all L list paths at once, and the warps of a CTA run their decoders in
+// lockstep (block barriers at every leaf and after every round; see Decoder). The decoding tree is expanded at compile time
 // (template recursion over (r_v, m_v, span offset)), so every node's size, lane mapping and
 // register arrays are static. Per warp, shared memory holds one LLR buffer per tree level
 // with L slots; list reselection never copies LLRs: each path keeps, per pending ancestor
 // level, the slot index of its ancestor's LLRs (shuffled from the parent lane on every list
 // step). Decided bits of finished nodes sit in a per-path packed bit buffer (double
-// buffered; a list step copies only the words left of the current node).
+// buffered; a list step copies only the words left of the current node); permuted nodes
+// un-permute them by gathering through the inverse maps the host stores with the maps.
 //
 // Exactness: the arithmetic is add, subtract, min, abs, negate, compare and multiply by 1/2.
 // On integer-valued LLRs below 2^24 / 2^m every intermediate value is an exactly
