@@ -483,17 +483,26 @@ struct Decoder {
             const int itp = __shfl_sync(kFull, pos[0], orig);
             const float lrb_o = __shfl_sync(kFull, lrb, orig);
             const float pflip = pm + r_o + (p ? -lrb_o : lrb_o);  // Eq. (4)
-            const int src = w.lane < 2 * L ? (w.lane >> 1) : 0;
-            const float kpm = __shfl_sync(kFull, pm, src);
-            const float fpm = __shfl_sync(kFull, pflip, src);
-            const float cpm = (w.lane & 1) ? fpm : kpm;
-            // rank of candidate `lane` among the 2L by (PM, 2l + flip)
+            // candidate c = 2l + flip; every group of 2L lanes holds all candidates and
+            // compares them against its share of the 2L, and the partial counts are summed
+            constexpr int NC = 2 * L;
+            constexpr int GRP = cmin(32 / NC, NC);  // lane groups sharing the comparisons
+            constexpr int Q = NC / GRP;             // comparisons per group
+            const int c = w.lane & (NC - 1);
+            const int grp = (w.lane / NC) % GRP;
+            const float kpm = __shfl_sync(kFull, pm, c >> 1);
+            const float fpm = __shfl_sync(kFull, pflip, c >> 1);
+            const float cpm = (c & 1) ? fpm : kpm;
+            // rank of candidate c among the 2L by (PM, 2l + flip)
             int rank = 0;
 #pragma unroll
-            for (int c2 = 0; c2 < 2 * L; c2++) {
+            for (int k = 0; k < Q; k++) {
+                const int c2 = grp * Q + k;
                 const float o = __shfl_sync(kFull, cpm, c2);
-                rank += (o < cpm) || (o == cpm && c2 < w.lane);
+                rank += (o < cpm) || (o == cpm && c2 < c);
             }
+#pragma unroll
+            for (int d = NC; d < NC * GRP; d <<= 1) rank += __shfl_xor_sync(kFull, rank, d);
             // candidate of rank q goes to path q
             if (w.lane < 2 * L && rank < L) sel[rank] = (uint8_t)w.lane;
             __syncwarp();
