@@ -553,23 +553,72 @@ struct Decoder {
         constexpr int C2 = 2 * L;
         constexpr int HALF = 1 << (S - 1);
         float mylm = 0.f;  // lane c keeps LM_c
+        if constexpr (M >= 9) {
+            // one candidate at a time with a warp sum each (a rolled loop: the m = 9 trees
+            // exceed the instruction caches, and the unrolled form below measured 2% slower)
 #pragma unroll 1
-        for (int c = 0; c < C2; c++) {
-            const uint16_t* r = recs + c * kRec;
-            const int a = r[S - 1];
-            const int h = 31 - __clz(a);
-            const int lorg = c & (L - 1);
-            float acc = 0.f;
+            for (int c = 0; c < C2; c++) {
+                const uint16_t* r = recs + c * kRec;
+                const int a = r[S - 1];
+                const int h = 31 - __clz(a);
+                const int lorg = c & (L - 1);
+                float acc = 0.f;
 #pragma unroll
-            for (int t = 0; t < (HALF + 31) / 32; t++) {
-                const int jp = w.lane + 32 * t;
-                if (jp < HALF) {
-                    const int j = insert_zero(jp, h);
-                    acc += fminf(fabsf(src(lorg, j)), fabsf(src(lorg, j ^ a)));
+                for (int t = 0; t < (HALF + 31) / 32; t++) {
+                    const int jp = w.lane + 32 * t;
+                    if (jp < HALF) {
+                        const int j = insert_zero(jp, h);
+                        acc += fminf(fabsf(src(lorg, j)), fabsf(src(lorg, j ^ a)));
+                    }
+                }
+                acc = warp_sum(acc);
+                if (w.lane == c) mylm = acc;
+            }
+        } else {
+            // smaller trees: every lane's partial LM of every candidate ...
+            constexpr int LG = cilog2(C2);
+            float part[C2];
+#pragma unroll
+            for (int c = 0; c < C2; c++) {
+                const uint16_t* r = recs + c * kRec;
+                const int a = r[S - 1];
+                const int h = 31 - __clz(a);
+                const int lorg = c & (L - 1);
+                float acc = 0.f;
+#pragma unroll
+                for (int t = 0; t < (HALF + 31) / 32; t++) {
+                    const int jp = w.lane + 32 * t;
+                    if (jp < HALF) {
+                        const int j = insert_zero(jp, h);
+                        acc += fminf(fabsf(src(lorg, j)), fabsf(src(lorg, j ^ a)));
+                    }
+                }
+                part[c] = acc;
+            }
+            // ... reduced and scattered over the butterfly d = 16, 8, ..., 1: the first LG stages
+            // halve the candidates a lane holds (it keeps one half and adds the partner's copy of
+            // it), the rest add across lanes holding the same candidate. Every addition is the one
+            // a warp sum of that candidate's partials makes, so the totals are bitwise equal to it.
+#pragma unroll
+            for (int st = 0; st < 5; st++) {
+                const int d = 16 >> st;
+                if (st < LG) {
+                    const int n = C2 >> st;  // candidates held before this stage
+                    const bool up = (w.lane & d) != 0;
+#pragma unroll
+                    for (int k = 0; k < C2 / 2; k++) {
+                        if (k < n / 2) {
+                            const float keep = up ? part[k + n / 2] : part[k];
+                            const float give = up ? part[k] : part[k + n / 2];
+                            part[k] = keep + __shfl_xor_sync(kFull, give, d);
+                        }
+                    }
+                } else {
+                    part[0] += __shfl_xor_sync(kFull, part[0], d);
                 }
             }
-            acc = warp_sum(acc);
-            if (w.lane == c) mylm = acc;
+            // lanes with (lane >> (5 - LG)) == c hold LM_c; lane c < C2 takes it
+            mylm = __shfl_sync(kFull, part[0], (w.lane & (C2 - 1)) << (5 - LG));
         }
         // rank of candidate `lane` by (LM descending, c ascending); lane q < L takes rank q
         int rank = 0;
