@@ -554,9 +554,9 @@ struct Decoder {
         constexpr int HALF = 1 << (S - 1);
         float mylm = 0.f;  // lane c keeps LM_c
         if constexpr (M >= 9) {
-            // one candidate at a time with a warp sum each (a rolled loop: the m = 9 trees
-            // exceed the instruction caches, and the unrolled form below measured 2% slower)
-#pragma unroll 1
+            // candidates two at a time, each with a warp sum (the m = 9 trees exceed the
+            // instruction caches: the fully unrolled form below measured 2% slower there)
+#pragma unroll 2
             for (int c = 0; c < C2; c++) {
                 const uint16_t* r = recs + c * kRec;
                 const int a = r[S - 1];
