@@ -702,7 +702,7 @@ struct Decoder {
                     }
                 }
             } else if constexpr (H >= 32) {
-#pragma unroll 1
+#pragma unroll 4  // independent paths: 4 chains in flight
                 for (int l = 0; l < L; l++)
 #pragma unroll
                     for (int t = 0; t < H / 32; t++) {
@@ -742,7 +742,7 @@ struct Decoder {
                 }
             } else if constexpr (H >= 32) {
                 static_assert(OFF % 32 == 0, "spans of 64 or more bits are word aligned");
-#pragma unroll 1
+#pragma unroll 4
                 for (int l = 0; l < L; l++) {
                     const int sl = __shfl_sync(kFull, ps.slot[S], l);
                     const uint32_t* bl = bitbuf(w, w.bsel, l) + OFF / 32;
