@@ -365,9 +365,7 @@ struct Decoder {
                     if (used == DEPTH && q + 1 < L) {
                         // rare: both cached candidates were taken; rescan the untaken ones
                         bool h1 = false, h2 = false;
-#pragma unroll
-                        for (int e = 0; e < E; e++) {
-                            const float a = v[e];
+                        auto visit = [&](int e, float a) {
                             const bool ok = !((taken >> e) & 1);
                             const bool g1 = ok && (!h1 || fabsf(a) > fabsf(c1));
                             const bool g2 = ok && !g1 && (!h2 || fabsf(a) > fabsf(c2));
@@ -377,6 +375,20 @@ struct Decoder {
                             c1 = g1 ? a : c1;
                             e1 = g1 ? e : e1;
                             h1 = h1 || g1;
+                        };
+                        if constexpr (M >= 9 && L <= 4) {
+                            // from a local copy with a rolled loop: 16% less code for the
+                            // m = 9 trees, whose code exceeds the instruction caches (measured
+                            // +1%); with L = 8 rescans are frequent enough, and smaller trees
+                            // fit the caches, so the unrolled form below is faster there
+                            float vloc[E];
+#pragma unroll
+                            for (int e = 0; e < E; e++) vloc[e] = v[e];
+#pragma unroll 1
+                            for (int e = 0; e < E; e++) visit(e, vloc[e]);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < E; e++) visit(e, v[e]);
                         }
                         avail = (h1 ? 1 : 0) + (h2 ? 1 : 0);
                         used = 0;
