@@ -69,3 +69,20 @@ def test_graph_replays_match_direct_decoding():
     torch.cuda.synchronize()
     assert torch.equal(host_out, d.decode(host_in.cuda()).cpu())
     g.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("m,r,P,L", [(9, 2, 20, 4), (7, 2, 8, 4), (9, 3, 16, 8)])
+def test_launch_size_never_changes_results(m, r, P, L):
+    """Launches of a few waves run in wider shapes than large ones; every frame must decode
+    the same whatever batch it is part of."""
+    d = pkg.Decoder(m, r, P, L, perm_seed=9)
+    big = 6000
+    fr = I.make_frames(m, r, big, 2.5, seed=12)
+    x = torch.from_numpy(fr["llr"].astype(np.float32)).cuda()
+    ref = d.decode(x).cpu()
+    off = 0
+    for n in (1, 3, 37, 152, 700, 1500, 3000):
+        n = min(n, big - off)
+        assert torch.equal(d.decode(x[off:off + n]).cpu(), ref[off:off + n]), n
+        off += n
