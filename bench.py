@@ -259,25 +259,48 @@ PAPER_FER = {"p-FHT-FSCL-4-20": {1.0: 9.80e-3, 1.5: 2.11e-3, 2.0: 2.99e-4, 2.5: 
              "Aut-SSC-512": {1.0: 9.38e-3, 1.5: 2.14e-3, 2.0: 2.58e-4, 2.5: 2.76e-5}}
 
 
+# FER sweeps of the paper's configurations: (m, r, P, L, [(run name, dtype, decoder kind)],
+# default Eb/N0 points)
+SWEEPS = {
+    "rm29": (9, 2, 20, 4, [("p-FHT-FSCL-4-20", "f32", "pfht"), ("p-FHT-FSCL-4-20 FP16 LLRs", "f16", "pfht"),
+                           ("p-FHT-FSCL-4-20 INT8 LLRs", "i8", "pfht"), ("Aut-SSC-512", "f32", "autssc")],
+             [1.0, 1.5, 2.0, 2.25, 2.5]),
+    "rm27": (7, 2, 8, 4, [("p-FHT-FSCL-4-8", "f32", "pfht"), ("p-FHT-FSCL-4-8 INT8 LLRs", "i8", "pfht")],
+             [1.0, 1.5, 2.0, 2.5, 3.0, 3.5, 4.0, 4.5, 5.0]),
+    "rm39": (9, 3, 16, 8, [("p-FHT-FSCL-8-16", "f32", "pfht"), ("p-FHT-FSCL-8-16 FP16 LLRs", "f16", "pfht")],
+             [1.0, 1.5, 2.0, 2.5, 3.0]),  # no frame errors in 10^6 frames per point from 3 dB up
+}
+
+
 def run_fer_sweep(args):
-    """FER of p-FHT-FSCL-4-20 (FP32, FP16 and INT8 LLRs) and Aut-SSC-512 on the same RM(2,9)
-    frames, generated on the GPU in chunks, with decoding time per point."""
+    """FER of p-FHT-FSCL on the paper's configurations (RM(2,9) P=20 L=4 in FP32, FP16 and
+    INT8 beside Aut-SSC-512; RM(2,7) P=8 L=4 in FP32 and INT8; RM(3,9) P=16 L=8 in FP32 and
+    FP16), every decoder on the same frames, generated on the GPU in chunks, with decoding
+    time per point and the rate of decisions differing from the FP32 decoder's."""
     import torch
 
     import paper_2108_12550_gb300 as pkg
 
-    m, r, k = 9, 2, 46
-    pf = pkg.Decoder(m, r, 20, 4, perm_seed=1)
-    pf16 = pkg.Decoder(m, r, 20, 4, perm_seed=1, dtype="f16")
-    pf8 = pkg.Decoder(m, r, 20, 4, perm_seed=1, dtype="i8")
-    ssc = pkg.Decoder(m, r, 512, algo="autssc", perm_seed=1)
+    m, r, P, L, spec, default_eb = SWEEPS[args.sweep_code]
+    k = I.rm_dims(m, r)[1]
+    kw = (k + 31) // 32
+    if args.ebn0 is None:
+        args.ebn0 = default_eb
+
+    def convert(dt):
+        if dt == "f16":
+            return lambda x: x.half()
+        if dt == "i8":
+            return lambda x: torch.clamp(torch.round(x / 0.25), -127, 127).to(torch.int8)
+        return lambda x: x
+
+    runs = [(name, pkg.Decoder(m, r, 512, algo="autssc", perm_seed=1) if kind == "autssc"
+             else pkg.Decoder(m, r, P, L, perm_seed=1, dtype=dt), convert(dt)) for name, dt, kind in spec]
+    fp32_name = spec[0][0]
     gen = torch.Generator(device="cuda")
     chunk = 1 << 18
-    out = torch.empty((chunk, 2), dtype=torch.int32, device="cuda")
-    ref_bits = torch.empty((chunk, 2), dtype=torch.int32, device="cuda")
-    runs = [("p-FHT-FSCL-4-20", pf, lambda x: x), ("p-FHT-FSCL-4-20 FP16 LLRs", pf16, lambda x: x.half()),
-            ("p-FHT-FSCL-4-20 INT8 LLRs", pf8, lambda x: torch.clamp(torch.round(x / 0.25), -127, 127).to(torch.int8)),
-            ("Aut-SSC-512", ssc, lambda x: x)]
+    out = torch.empty((chunk, kw), dtype=torch.int32, device="cuda")
+    ref_bits = torch.empty((chunk, kw), dtype=torch.int32, device="cuda")
     # Chunk c of point Eb/N0 draws its frames from its own seed, so chunks are independent and
     # a sweep can stop and resume: --checkpoint keeps one JSON line per finished chunk.
     done_chunks = {}
@@ -285,7 +308,7 @@ def run_fer_sweep(args):
         with open(args.checkpoint) as fh:
             for line in fh:
                 rec = json.loads(line)
-                done_chunks[(rec["ebn0_db"], rec["chunk"])] = rec
+                done_chunks[(rec.get("code", "rm29"), rec["ebn0_db"], rec["chunk"])] = rec
     ckpt = open(args.checkpoint, "a") if args.checkpoint else None
     points = []
     for eb in args.ebn0:
@@ -297,12 +320,13 @@ def run_fer_sweep(args):
         t_dec = {name: 0.0 for name, _, _ in runs}
         for ci, done in enumerate(range(0, n_pf, chunk)):
             f = min(chunk, n_pf - done)
-            rec = done_chunks.get((eb, ci))
+            rec = done_chunks.get((args.sweep_code, eb, ci))
             if rec is None or rec["frames"] != f:
                 gen.manual_seed(2108 * 1000003 + int(round(eb * 1000)) * 65537 + ci)
                 u, llr = I.make_frames_torch(m, r, f, eb, gen)
-                unpack = lambda w: ((w.view(-1, 2, 1) >> torch.arange(32, device="cuda")) & 1).view(-1, 64)[:, :k]
-                rec = {"ebn0_db": eb, "chunk": ci, "frames": f, "errors": {}, "differ": {}, "seconds": {}}
+                unpack = lambda w: ((w.view(-1, kw, 1) >> torch.arange(32, device="cuda")) & 1).view(-1, 32 * kw)[:, :k]
+                rec = {"code": args.sweep_code, "ebn0_db": eb, "chunk": ci, "frames": f, "errors": {}, "differ": {},
+                       "seconds": {}}
                 for name, dec, conv in runs:
                     if done >= lims[name]:
                         continue
@@ -315,7 +339,7 @@ def run_fer_sweep(args):
                     torch.cuda.synchronize()
                     rec["seconds"][name] = e0.elapsed_time(e1) * 1e-3
                     rec["errors"][name] = int(torch.any(unpack(out[:g]).to(torch.uint8) != u[:g], dim=1).sum().item())
-                    if name == "p-FHT-FSCL-4-20":
+                    if name == fp32_name:
                         ref_bits[:g].copy_(out[:g])
                     elif name.startswith("p-FHT"):
                         rec["differ"][name] = int(torch.any(out[:g] != ref_bits[:g], dim=1).sum().item())
@@ -333,13 +357,13 @@ def run_fer_sweep(args):
                         "frames_per_s": n / t_dec[name] if t_dec[name] else None}
             if name in PAPER_FER:
                 pt[name]["paper_fer"] = PAPER_FER[name].get(eb)
-            if name.startswith("p-FHT") and name != "p-FHT-FSCL-4-20":
+            if name.startswith("p-FHT") and name != fp32_name:
                 pt[name]["decisions_differing_from_fp32"] = differ[name] / n
         points.append(pt)
         print(json.dumps(pt), flush=True)
     if ckpt:
         ckpt.close()
-    print(json.dumps({"metric": "FER RM(2,9): p-FHT-FSCL-4-20 (FP32/FP16/INT8 LLRs) vs Aut-SSC-512 on the same frames",
+    print(json.dumps({"metric": f"FER RM({r},{m}) P={P} L={L}: " + ", ".join(n for n, _, _ in spec) + " on the same frames",
                       "points": points, "data": "synthetic BPSK/AWGN frames generated on the GPU"}), flush=True)
 
 
@@ -350,7 +374,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="rm29_p20_l4", choices=sorted(WORKLOADS) + ["serving_mix", "fer_sweep"])
-    ap.add_argument("--ebn0", type=float, nargs="+", default=[1.0, 1.5, 2.0, 2.25, 2.5],
+    ap.add_argument("--sweep-code", default="rm29", choices=sorted(SWEEPS), help="FER sweep: configuration")
+    ap.add_argument("--ebn0", type=float, nargs="+", default=None,
                     help="FER sweep: Eb/N0 points (dB)")
     ap.add_argument("--sweep-frames", type=int, default=1 << 22, help="FER sweep: frames per point")
     ap.add_argument("--ssc-frames", type=int, default=1 << 20, help="FER sweep: Aut-SSC frames per point")
