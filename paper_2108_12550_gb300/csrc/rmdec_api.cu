@@ -29,6 +29,7 @@ constexpr int kRec = 11;
 constexpr uint32_t kPermTag = 0x5045524Du;     // 'PERM'
 constexpr uint32_t kSscStream = 0x53534300u;   // 'SSC\0'
 constexpr int kMaxTickets = 1024;
+constexpr int kHostChunks = 4;  // rmdec_decode_host: chunks of a large batch (upload/decode overlap)
 
 // ------------------------------------------------------------ Philox4x32-10 ---
 // Counter-based generator of Salmon, Moraes, Dror, Shaw (SC'11): ten rounds of two
@@ -168,6 +169,8 @@ struct rmdec_ctx {
     std::vector<size_t> smem_w;      // dynamic shared memory for W warps per CTA
     void* d_stage = nullptr;
     size_t stage_bytes = 0;
+    cudaStream_t copy_stream = nullptr;       // rmdec_decode_host's uploads of large batches
+    cudaEvent_t chunk_ev[kHostChunks + 1] = {};  // per-chunk upload done; [kHostChunks]: start
     std::map<uint64_t, cudaEvent_t> tickets;
     uint64_t next_ticket = 1;
     std::string err;
@@ -506,6 +509,12 @@ void rmdec_destroy(rmdec_t h) {
     if (h->d_recs) cudaFree(h->d_recs);
     if (h->d_info) cudaFree(h->d_info);
     if (h->d_stage) cudaFree(h->d_stage);
+    if (h->copy_stream) {
+        cudaStreamSynchronize(h->copy_stream);
+        cudaStreamDestroy(h->copy_stream);
+    }
+    for (auto& ev : h->chunk_ev)
+        if (ev) cudaEventDestroy(ev);
     delete h;
 }
 
@@ -584,9 +593,42 @@ rmdec_status rmdec_decode_host(rmdec_t h, const void* llr_host, int64_t n_frames
     cudaStream_t s = (cudaStream_t)stream;
     uint8_t* d_in = static_cast<uint8_t*>(h->d_stage);
     uint32_t* d_out = reinterpret_cast<uint32_t*>(d_in + in_pad);
-    if ((e = cudaMemcpyAsync(d_in, llr_host, in_bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess) return h->cuda_fail(e, "H2D");
-    rmdec_status st = launch(h, d_in, n_frames, d_out, nullptr, nullptr, nullptr, s);
+    rmdec_status st = ensure_device(h);
+    if (st == RMDEC_OK) st = configure_shape(h);
     if (st != RMDEC_OK) return st;
+    // Large batches go in chunks of at least 8 waves: chunk c + 1 is uploaded on the handle's
+    // copy stream while chunk c decodes on `stream`, each decode waiting for its chunk's upload.
+    const int64_t wave = (int64_t)h->sm_count * h->blocks_per_sm;
+    const int chunks = n_frames >= 32 * wave ? kHostChunks : n_frames >= 16 * wave ? 2 : 1;
+    if (chunks == 1) {
+        if ((e = cudaMemcpyAsync(d_in, llr_host, in_bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess) return h->cuda_fail(e, "H2D");
+        st = launch(h, d_in, n_frames, d_out, nullptr, nullptr, nullptr, s);
+        if (st != RMDEC_OK) return st;
+    } else {
+        if (!h->copy_stream) {
+            if ((e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking)) != cudaSuccess) return h->cuda_fail(e, "copy stream");
+            for (auto& ev : h->chunk_ev)
+                if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return h->cuda_fail(e, "chunk events");
+        }
+        // uploads start after the work already queued on `stream` (which may read the buffer)
+        if ((e = cudaEventRecord(h->chunk_ev[kHostChunks], s)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(h->copy_stream, h->chunk_ev[kHostChunks], 0)) != cudaSuccess)
+            return h->cuda_fail(e, "copy stream order");
+        const size_t fb = (size_t)h->n * llr_elem_bytes(h->dtype), ow = (size_t)((h->k + 31) / 32);
+        for (int c = 0; c < chunks; c++) {
+            const int64_t f0 = n_frames * c / chunks, f1 = n_frames * (c + 1) / chunks;
+            if ((e = cudaMemcpyAsync(d_in + (size_t)f0 * fb, static_cast<const uint8_t*>(llr_host) + (size_t)f0 * fb,
+                                     (size_t)(f1 - f0) * fb, cudaMemcpyHostToDevice, h->copy_stream)) != cudaSuccess ||
+                (e = cudaEventRecord(h->chunk_ev[c], h->copy_stream)) != cudaSuccess)
+                return h->cuda_fail(e, "H2D");
+        }
+        for (int c = 0; c < chunks; c++) {
+            const int64_t f0 = n_frames * c / chunks, f1 = n_frames * (c + 1) / chunks;
+            if ((e = cudaStreamWaitEvent(s, h->chunk_ev[c], 0)) != cudaSuccess) return h->cuda_fail(e, "chunk order");
+            st = launch(h, d_in + (size_t)f0 * fb, f1 - f0, d_out + (size_t)f0 * ow, nullptr, nullptr, nullptr, s);
+            if (st != RMDEC_OK) return st;
+        }
+    }
     if ((e = cudaMemcpyAsync(bits_out_host, d_out, out_bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return h->cuda_fail(e, "D2H");
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return h->cuda_fail(e, "synchronize");
     return RMDEC_OK;

@@ -86,3 +86,20 @@ def test_launch_size_never_changes_results(m, r, P, L):
         n = min(n, big - off)
         assert torch.equal(d.decode(x[off:off + n]).cpu(), ref[off:off + n]), n
         off += n
+
+
+@pytest.mark.gpu
+def test_large_host_decode_in_chunks_matches_device_decode():
+    """rmdec_decode_host splits batches of 16+ waves into chunks whose uploads overlap the
+    previous chunk's decode; the bits must equal one device-resident decode."""
+    m, r, P, L = 5, 2, 4, 2
+    d = pkg.Decoder(m, r, P, L, perm_seed=13)
+    w, c = d.get_tuning()
+    n = 40 * 152 * c + 123  # more than 32 waves of the default shape on a 152-SM GPU, ragged
+    fr = I.make_frames(m, r, 4096, 3.0, seed=14)
+    x = np.tile(fr["llr"].astype(np.float32), (n // 4096 + 1, 1))[:n]
+    host_in = torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    host_out = torch.zeros((n, d.kw), dtype=torch.int32).pin_memory()
+    d.decode_host(host_in, host_out)
+    ref = d.decode(host_in.cuda()).cpu()
+    assert torch.equal(host_out, ref)
