@@ -113,9 +113,12 @@ rmdec_status rmdec_decode_debug(rmdec_t h, const void *llr_dev, int64_t n_frames
                                 uint32_t *cw_out_dev, float *pm_out_dev, int32_t *best_out_dev, void *stream);
 
 /* End-to-end decode from and to HOST memory: copies the LLRs in, decodes, copies the bits
- * out, all on `stream`, and returns after the stream work has completed. Pinned host
- * buffers give full copy bandwidth; pageable ones work but are staged by the driver.
- * Uses a handle-owned device staging area grown on demand. */
+ * out, and returns after the work has completed. Decoding and the copy back run on `stream`;
+ * batches of 16 or more waves of the launch shape are uploaded in 2-8 chunks on a
+ * handle-owned copy stream that runs ahead of the decodes (each chunk's decode waits for its
+ * upload), so uploads overlap decoding. Pinned host buffers give full copy bandwidth and the
+ * overlap; pageable ones work but are staged by the driver. Uses a handle-owned device
+ * staging area grown on demand. */
 rmdec_status rmdec_decode_host(rmdec_t h, const void *llr_host, int64_t n_frames, uint32_t *bits_out_host,
                                void *stream);
 

@@ -29,7 +29,7 @@ constexpr int kRec = 11;
 constexpr uint32_t kPermTag = 0x5045524Du;     // 'PERM'
 constexpr uint32_t kSscStream = 0x53534300u;   // 'SSC\0'
 constexpr int kMaxTickets = 1024;
-constexpr int kHostChunks = 4;  // rmdec_decode_host: chunks of a large batch (upload/decode overlap)
+constexpr int kHostChunks = 8;  // rmdec_decode_host: chunks of a large batch (upload/decode overlap)
 
 // ------------------------------------------------------------ Philox4x32-10 ---
 // Counter-based generator of Salmon, Moraes, Dror, Shaw (SC'11): ten rounds of two
@@ -599,7 +599,7 @@ rmdec_status rmdec_decode_host(rmdec_t h, const void* llr_host, int64_t n_frames
     // Large batches go in chunks of at least 8 waves: chunk c + 1 is uploaded on the handle's
     // copy stream while chunk c decodes on `stream`, each decode waiting for its chunk's upload.
     const int64_t wave = (int64_t)h->sm_count * h->blocks_per_sm;
-    const int chunks = n_frames >= 32 * wave ? kHostChunks : n_frames >= 16 * wave ? 2 : 1;
+    const int chunks = n_frames >= 64 * wave ? kHostChunks : n_frames >= 32 * wave ? 4 : n_frames >= 16 * wave ? 2 : 1;
     if (chunks == 1) {
         if ((e = cudaMemcpyAsync(d_in, llr_host, in_bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess) return h->cuda_fail(e, "H2D");
         st = launch(h, d_in, n_frames, d_out, nullptr, nullptr, nullptr, s);
