@@ -31,7 +31,7 @@ struct GroupDec {
     const uint16_t* info;  // K information positions
     int cfg;               // group_cfg_index(m, r)
     int P, K;
-    int rec_elems;         // NREC * kRec: forward map elements per decoder
+    int rec_elems;         // SMEM_NREC * kRec: forward map elements per decoder in shared memory
     int dtype;
     float qclamp;
     int single;

@@ -80,7 +80,14 @@ struct Cfg {
         for (int t = MIN_DEEP; t < s; t++) o += lvl_floats(t);
         return o;
     }
-    static constexpr int ALPHA_FLOATS = alt_off(M);
+    // LEAN: RM(3, m >= 8), whose warp areas limit the resident warps (shared memory, not
+    // registers). The one deeper permuted level (m - 1) then needs no second buffer: its
+    // unpermuted LLRs are staged in the lower levels' buffers, which hold nothing yet when
+    // the left spine reaches it, and the permuted copies go to the level's own buffer. The
+    // permutation maps are read from the device table (L1) instead of block shared memory.
+    static constexpr bool LEAN = NLEV == 2 && M >= 8 && lvl_off(MIN_DEEP) >= lvl_floats(MIN_DEEP);
+    static constexpr int SMEM_NREC = LEAN ? 0 : NREC;  // maps per decoder in block shared memory
+    static constexpr int ALPHA_FLOATS = LEAN ? MAIN_FLOATS : alt_off(M);
     static constexpr int BITS_WORDS = 2 * L * NW;  // double-buffered per-path bit buffers
     // warp area: alpha | bits | xtmp (NW) | best codeword (NW) | spc order (L*32 bytes)
     static constexpr int OFF_BITS = ALPHA_FLOATS * 4;
@@ -98,7 +105,7 @@ struct Warp {
     uint32_t* best;     // NW: this warp's best codeword so far
     uint8_t* spc;       // L x 32 SPC order scratch
     const float* y;     // frame LLRs
-    const uint16_t* rec;      // this decoder's NREC records (shared memory)
+    const uint16_t* rec;      // this decoder's NREC records (shared memory; LEAN: device table)
     const uint16_t* rec_inv;  // their inverse maps (global memory; read only to un-permute)
     int lane;
     int bsel;           // current bit buffer (warp uniform)
@@ -664,7 +671,9 @@ struct Decoder {
             const uint16_t* lrec = w.rec + LEVEL * 2 * L * kRec;
             // LLRs of this node for path l at position j
             // a deeper permuted node keeps its permuted copy in the level's second buffer
-            const float* nodebuf = w.alpha + ((PERM && !ROOT) ? C::alt_off(S) : C::lvl_off(S));
+            // (LEAN: in the level's own buffer, the unpermuted LLRs staged below)
+            constexpr bool ALT = PERM && !ROOT && !C::LEAN;
+            const float* nodebuf = w.alpha + (ALT ? C::alt_off(S) : C::lvl_off(S));
             constexpr int STN = C::stride(S);
             if constexpr (ROOT) {
                 // every path's LLRs are y, so candidate c's permuted LLRs are y through the
@@ -679,12 +688,22 @@ struct Decoder {
                 const float npm = __shfl_sync(kFull, ps.pm, (w.lane < L ? c : 0) & (L - 1));
                 reselect<OFF, PEND>(w, ps, c % L, npm);
                 ps.selc[S] = c;
-                float* dst = w.alpha + C::alt_off(S);
+                const float* from = src;
+                if constexpr (C::LEAN) {
+                    // stage the L unpermuted paths in the lower levels' buffers (offset 0, free
+                    // until the first descent below this level; lvl_off(S) >= L * STN floats)
+                    float* stage = w.alpha;
+#pragma unroll 4
+                    for (int i = w.lane; i < L * STN; i += 32) stage[i] = src[i];
+                    __syncwarp();
+                    from = stage;
+                }
+                float* dst = w.alpha + (C::LEAN ? C::lvl_off(S) : C::alt_off(S));
 #pragma unroll 1
                 for (int q = 0; q < L; q++) {
                     const int cq = __shfl_sync(kFull, c, q);
                     const uint16_t* r = lrec + cq * kRec;
-                    const float* s_src = src + (cq % L) * STN;
+                    const float* s_src = from + (cq % L) * STN;
                     const int base = ga_lane_base(r, S, w.lane);
 #pragma unroll
                     for (int t = 0; t < ((1 << S) + 31) / 32; t++) {
@@ -898,7 +917,8 @@ struct Decoder {
     }
 };
 
-// Block shared memory, common to every configuration: the decoders' permutation records,
+// Block shared memory, common to every configuration: the decoders' permutation records
+// (SMEM_NREC per decoder),
 // the K information positions, the frame LLRs, per-warp (metric, decoder) reduction slots,
 // then one area of warp_stride bytes per warp.
 __host__ __device__ constexpr int frame_fixed_bytes(int rec_elems, int K, int N, int W) {
@@ -907,7 +927,7 @@ __host__ __device__ constexpr int frame_fixed_bytes(int rec_elems, int K, int N,
 
 template <int M, int R, int L>
 __host__ constexpr int Cfg<M, R, L>::fixed_bytes(int P, int K, int W) {
-    return frame_fixed_bytes(P * NREC * kRec, K, N, W);
+    return frame_fixed_bytes(P * SMEM_NREC * kRec, K, N, W);
 }
 
 // The forward maps of P decoders (per decoder `per` elements, followed in the device table by
@@ -947,8 +967,8 @@ struct FrameJob {
 };
 
 // Decodes frame f of a job with the whole block (Algorithm 5 over the P decoders, split
-// round-robin over the warps). The block's records and information positions must already
-// be in shared memory; the first barrier also publishes them. LOCK: see Decoder.
+// round-robin over the warps). The block's records (unless LEAN) and information positions
+// must already be in shared memory; the first barrier also publishes them. LOCK: see Decoder.
 template <int M, int R, int L, bool LOCK>
 __device__ __forceinline__ void decode_frame(const FrameJob& j, const FrameSmem& sm, int64_t f) {
     using C = Cfg<M, R, L>;
@@ -1001,7 +1021,7 @@ __device__ __forceinline__ void decode_frame(const FrameJob& j, const FrameSmem&
         const int p = p0 + warp;
         if (LOCK || p < j.P) {
             const int pr = p < j.P ? p : j.P - 1;
-            w.rec = sm.rec + pr * C::NREC * kRec;
+            w.rec = C::LEAN ? j.recs + 2 * pr * C::NREC * kRec : sm.rec + pr * C::NREC * kRec;
             w.rec_inv = j.recs + (2 * pr + 1) * C::NREC * kRec;
             int c0;
             const float pm = D::run(w, c0);
@@ -1075,9 +1095,9 @@ template <int M, int R, int L>
 __global__ void __launch_bounds__(32 * kMaxWarps, 1) pfht_kernel(LaunchArgs args) {
     using C = Cfg<M, R, L>;
     extern __shared__ __align__(16) uint8_t smem[];
-    const int rec_elems = args.P * C::NREC * kRec;
+    const int rec_elems = args.P * C::SMEM_NREC * kRec;
     const FrameSmem sm = carve_smem(smem, rec_elems, args.K, C::WARP_BYTES);
-    copy_maps(sm.rec, args.recs, args.P, C::NREC * kRec);
+    copy_maps(sm.rec, args.recs, args.P, C::SMEM_NREC * kRec);
     for (int i = threadIdx.x; i < args.K; i += blockDim.x) sm.info[i] = args.info[i];
     FrameJob j;
     j.recs = args.recs;

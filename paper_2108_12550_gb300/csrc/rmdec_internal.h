@@ -23,7 +23,7 @@ size_t llr_elem_bytes_of(rmdec_ctx* h);
 struct KernelEntry {
     const void* fn = nullptr;  // __global__ function
     int warp_bytes = 0;        // shared memory per warp
-    int nrec = 0;              // permutation maps per decoder (the device table adds their inverses)
+    int nrec = 0;              // permutation maps per decoder held in block shared memory
     int (*fixed_bytes)(int P, int K, int W) = nullptr;
 };
 
@@ -47,7 +47,7 @@ struct MemberInfo {
     const uint16_t* d_recs = nullptr;  // valid after prepare
     const uint16_t* d_info = nullptr;
     int warp_bytes = 0;
-    int nrec = 0;  // device records per decoder
+    int nrec = 0;  // permutation maps per decoder held in block shared memory
     int device = -1;
     int64_t wave = 0;  // CTAs of the handle's own launch resident at once (valid after prepare)
 };
@@ -67,7 +67,7 @@ const void* group_kernel_l4();
     do {                                                                                 \
         e->fn = reinterpret_cast<const void*>(&rmdec_dev::pfht_kernel<M, R, L>);         \
         e->warp_bytes = rmdec_dev::Cfg<M, R, L>::WARP_BYTES;                             \
-        e->nrec = rmdec_dev::Cfg<M, R, L>::NREC;                                         \
+        e->nrec = rmdec_dev::Cfg<M, R, L>::SMEM_NREC;                                    \
         e->fixed_bytes = [](int P, int K, int W) {                                       \
             return rmdec_dev::Cfg<M, R, L>::fixed_bytes(P, K, W);                        \
         };                                                                               \
