@@ -37,7 +37,7 @@ WORKLOADS = {
 METRIC = "frames/s RM(2,9) P=20 L=4 at FER~1e-4 Eb/N0"
 # DRAM bytes per frame from the ncu capture summarised in profiles/pfht_kernel_rm29_p20_l4.md,
 # valid only for the kernel code it was taken on (kernel_fingerprint() prefix)
-TRAFFIC = {"rm29_p20_l4": {"bytes_per_frame": (37054720 + 1189120) / 16384, "kernel_code_sha256": "17b10013a1e13ae7"}}
+TRAFFIC = {"rm29_p20_l4": {"bytes_per_frame": (37077504 + 1212672) / 16384, "kernel_code_sha256": "168da8f3e1f977a3"}}
 SMS = 152
 LANES_PER_SM = 128
 
