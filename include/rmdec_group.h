@@ -57,8 +57,11 @@ rmdec_status rmdec_group_decode(rmdec_group_t g, const rmdec_segment *segs, int 
  * CTAs; < 0: none, every segment is grouped). Never changes results. */
 rmdec_status rmdec_group_set_split(rmdec_group_t g, int64_t min_frames_alone);
 
-/* Launch shape of the group's launches: warps per CTA (1..4, 0 = the most resident warps)
- * and a cap on CTAs per SM (0 = the occupancy limit). Never changes results. */
+/* Launch shape of the group's launches: warps per CTA (1..20) and a cap on CTAs per SM
+ * (0 = the occupancy limit). 0 warps = the default: the CTA of 1..4 warps with the most
+ * resident warps per SM, except that a launch of at most one wave of that shape takes the
+ * CTA of 1..20 warps whose busiest CTA runs the fewest decoder rounds (weighted by each code's
+ * work per decoder). Never changes results. */
 rmdec_status rmdec_group_set_tuning(rmdec_group_t g, int warps_per_cta, int ctas_per_sm);
 
 void rmdec_group_destroy(rmdec_group_t g);

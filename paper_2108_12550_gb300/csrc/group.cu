@@ -98,6 +98,35 @@ rmdec_status launch_grouped(rmdec_group* g, const rmdec_segment* segs, std::vect
             }
         }
     }
+    // Launches of at most one wave of that shape take the shape that minimises the busiest
+    // CTA's work instead: frames go round-robin over the grid, so a CTA decodes at most
+    // ceil(n_s / grid) frames of segment s, each in ceil(P / W) rounds of one decoder of that
+    // code. (Measured on four codes at 50-200 frames each: 0.084 against 0.112 ms; at two or
+    // more waves the CTAs that finish early speed up the busiest one, which this count
+    // ignores, and the default shape measured faster.)
+    int64_t total_all = 0;
+    for (int i : order) total_all += segs[i].n_frames;
+    if (!g->req_warps && !g->req_ctas && total_all <= (int64_t)g->sm_count * occ_for(W)) {
+        auto busiest = [&](int c) {
+            const int o = occ_for(c);
+            if (o < 1) return 1e300;
+            const int64_t grid = std::min<int64_t>(total_all, (int64_t)g->sm_count * o);
+            double t = 0;
+            for (int i : order) {
+                const auto& m = mi[segs[i].decoder];
+                t += (double)((segs[i].n_frames + grid - 1) / grid) * ((m.P + c - 1) / c) * ((double)m.L * m.n * (m.m + m.r));
+            }
+            return t;
+        };
+        double best = busiest(W);
+        for (int c = 1; c <= kMaxWarps; c++) {
+            const double v = busiest(c);
+            if (v < best) {
+                best = v;
+                W = c;
+            }
+        }
+    }
     const int occ = occ_for(W);
     if (occ < 1) return g->fail(RMDEC_EINVAL, "group launch cannot be resident (%zu B shared memory)", smem_for(W));
     const int per_sm = g->req_ctas ? std::min(g->req_ctas, occ) : occ;
@@ -252,8 +281,8 @@ rmdec_status rmdec_group_set_split(rmdec_group_t g, int64_t min_frames_alone) {
 
 rmdec_status rmdec_group_set_tuning(rmdec_group_t g, int warps_per_cta, int ctas_per_sm) {
     if (!g) return RMDEC_EINVAL;
-    if (warps_per_cta < 0 || warps_per_cta > 4 || ctas_per_sm < 0)
-        return g->fail(RMDEC_EINVAL, "warps_per_cta must be 0..4 and ctas_per_sm >= 0");
+    if (warps_per_cta < 0 || warps_per_cta > rmdec_dev::kMaxWarps || ctas_per_sm < 0)
+        return g->fail(RMDEC_EINVAL, "warps_per_cta must be 0..%d and ctas_per_sm >= 0", rmdec_dev::kMaxWarps);
     g->req_warps = warps_per_cta;
     g->req_ctas = ctas_per_sm;
     return RMDEC_OK;

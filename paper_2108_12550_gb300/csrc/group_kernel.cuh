@@ -74,8 +74,10 @@ __device__ __forceinline__ void group_dispatch(int cfg, const FrameJob& j, const
     }
 }
 
+// Up to kMaxWarps warps per CTA (the host takes wide CTAs for launches of a few waves), with
+// the same per-thread register budget as pfht_kernel.
 template <int L>
-__global__ void __launch_bounds__(128, 5) group_kernel(const __grid_constant__ GroupArgs a) {
+__global__ void __launch_bounds__(32 * kMaxWarps, 1) group_kernel(const __grid_constant__ GroupArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
     const FrameSmem sm = carve_smem(smem, a.rec_cap, a.k_cap, a.warp_stride);
     int seg = 0, loaded = -1;

@@ -109,5 +109,7 @@ def test_group_membership_is_validated_on_the_host():
     assert lib.rmdec_group_decode(ok._h, seg, 1, None) == pkg.EINVAL  # misaligned LLRs
     assert b"aligned" in lib.rmdec_group_last_error(ok._h)
     assert lib.rmdec_group_decode(ok._h, None, 1, None) == pkg.EINVAL
-    assert lib.rmdec_group_set_tuning(ok._h, 5, 0) == pkg.EINVAL
+    assert lib.rmdec_group_set_tuning(ok._h, 21, 0) == pkg.EINVAL
+    assert lib.rmdec_group_set_tuning(ok._h, -1, 0) == pkg.EINVAL
+    assert lib.rmdec_group_set_tuning(ok._h, 20, 0) == pkg.OK
     ok.close()

@@ -93,10 +93,11 @@ def test_real_valued_group_equals_separate_decodes():
     outs = grp.decode(segs)
     for (di, x, _), out in zip(segs, outs):
         assert torch.equal(out, decs[di].decode(x))
-    # a different launch shape never changes results
-    grp.set_tuning(2, 1)
-    outs2 = grp.decode(segs)
-    assert all(torch.equal(a, b) for a, b in zip(outs, outs2))
+    # a different launch shape never changes results (narrow, and wider than some members' P)
+    for wq, cq in ((2, 1), (12, 0)):
+        grp.set_tuning(wq, cq)
+        outs2 = grp.decode(segs)
+        assert all(torch.equal(a, b) for a, b in zip(outs, outs2)), (wq, cq)
     grp.close()
 
 
