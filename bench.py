@@ -254,6 +254,60 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def run_grouped(args):
+    """Grouped multi-code launches against one launch per code: RM(2,7) P=8 INT8, RM(2,8) P=8,
+    RM(2,9) P=20, RM(3,9) P=8 INT8 (L = 4), at a few frames per code and at large segments
+    (which the default split sends to their own launches). CUDA-event times, best of 5."""
+    import torch
+
+    import paper_2108_12550_gb300 as pkg
+
+    specs = {"RM(2,9)": (9, 2, 20, "f32", 131072), "RM(2,7)": (7, 2, 8, "i8", 262144),
+             "RM(3,9)": (9, 3, 8, "i8", 32768), "RM(2,8)": (8, 2, 8, "f32", 131072)}
+    decs, xs = {}, {}
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    for i, (name, (m, r, P, dt, nf)) in enumerate(specs.items()):
+        decs[name] = pkg.Decoder(m, r, P, 4, perm_seed=i + 1, dtype=dt)
+        _, llr = I.make_frames_torch(m, r, nf, 2.5, gen)
+        if dt == "i8":
+            llr = torch.clamp(torch.round(llr / 0.25), -127, 127).to(torch.int8)
+        xs[name] = llr.contiguous()
+    torch.cuda.synchronize()
+
+    def best_ms(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return min(ts)
+
+    cases, same = [], True
+    mixes = {"four codes": ["RM(2,9)", "RM(2,7)", "RM(3,9)", "RM(2,8)"], "RM(2,.) codes": ["RM(2,9)", "RM(2,7)", "RM(2,8)"]}
+    for label, keys in mixes.items():
+        grp = pkg.Group([decs[k] for k in keys])
+        for nf in (50, 200, 600, None):
+            segs = [(i, xs[k][:nf] if nf else xs[k], None) for i, k in enumerate(keys)]
+            t_sep = best_ms(lambda: [decs[k].decode(x) for k, (_, x, _) in zip(keys, segs)])
+            t_grp = best_ms(lambda: grp.decode(segs))
+            outs = grp.decode(segs)
+            same = same and all(torch.equal(o, decs[k].decode(x)) for k, (_, x, _), o in zip(keys, segs, outs))
+            cases.append({"mix": label, "frames_per_code": nf or "large (" + ", ".join(str(xs[k].shape[0]) for k in keys) + ")",
+                          "grouped_ms": t_grp, "separate_ms": t_sep})
+        grp.close()
+    line = {"metric": "ms per decode of one segment per code: grouped launch vs one launch per code", "unit": "ms",
+            "n_gpus": 1, "higher_is_better": False, "dtype": "mixed i8/f32", "data": "synthetic, 2.5 dB",
+            "config": {"workload": "grouped_mix", "decoders": [f"{k} P={specs[k][2]} L=4 {specs[k][3]}" for k in specs]},
+            "cases": cases, "results_identical_grouped_and_separate": bool(same)}
+    print(json.dumps(line), flush=True)
+
+
 # Frame error rates printed in the paper's Fig. 6 (RM(2,9) panel) for comparison
 PAPER_FER = {"p-FHT-FSCL-4-20": {1.0: 9.80e-3, 1.5: 2.11e-3, 2.0: 2.99e-4, 2.5: 2.85e-5},
              "Aut-SSC-512": {1.0: 9.38e-3, 1.5: 2.14e-3, 2.0: 2.58e-4, 2.5: 2.76e-5}}
@@ -373,7 +427,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="rm29_p20_l4", choices=sorted(WORKLOADS) + ["serving_mix", "fer_sweep"])
+    ap.add_argument("--workload", default="rm29_p20_l4", choices=sorted(WORKLOADS) + ["serving_mix", "fer_sweep", "grouped_mix"])
     ap.add_argument("--sweep-code", default="rm29", choices=sorted(SWEEPS), help="FER sweep: configuration")
     ap.add_argument("--ebn0", type=float, nargs="+", default=None,
                     help="FER sweep: Eb/N0 points (dB)")
@@ -393,6 +447,8 @@ def main():
         return run_serving(args)
     if args.workload == "fer_sweep":
         return run_fer_sweep(args)
+    if args.workload == "grouped_mix":
+        return run_grouped(args)
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl)
