@@ -36,6 +36,11 @@ struct rmdec_group {
     int sm_count = 0, max_optin = 0;
     int req_warps = 0, req_ctas = 0;
     int64_t min_alone = 0;  // 0: one full wave of the decoder's own launch; < 0: never alone
+    // resident CTAs per SM for 0..kMaxWarps warps (-1: not computed yet) at the footprint
+    // (rec_cap, k_cap, n_cap, warp stride) of the last launch; occupancy queries cost host
+    // time on every small launch otherwise
+    int occ_key[4] = {-1, -1, -1, -1};
+    int occ_cache[rmdec_dev::kMaxWarps + 1];
     std::string err;
 
     rmdec_status fail(rmdec_status st, const char* fmt, ...) {
@@ -79,12 +84,22 @@ rmdec_status launch_grouped(rmdec_group* g, const rmdec_segment* segs, std::vect
         if ((e = cudaFuncSetAttribute(g->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, g->max_optin)) != cudaSuccess)
             return g->fail(RMDEC_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
         g->device = dev;
+        std::fill(g->occ_key, g->occ_key + 4, -1);  // occupancies are per device
     }
     auto smem_for = [&](int W) { return (size_t)frame_fixed_bytes(rec_cap, k_cap, n_cap, W) + 16 + (size_t)W * stride; };
+    const int key[4] = {rec_cap, k_cap, n_cap, stride};
+    if (!std::equal(key, key + 4, g->occ_key)) {
+        std::copy(key, key + 4, g->occ_key);
+        std::fill(g->occ_cache, g->occ_cache + kMaxWarps + 1, -1);
+    }
     auto occ_for = [&](int W) {
-        int o = 0;
-        if (smem_for(W) > (size_t)g->max_optin) return 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, g->fn, 32 * W, smem_for(W)) != cudaSuccess) return 0;
+        int& o = g->occ_cache[W];
+        if (o < 0) {
+            o = 0;
+            if (smem_for(W) <= (size_t)g->max_optin &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, g->fn, 32 * W, smem_for(W)) != cudaSuccess)
+                o = 0;
+        }
         return o;
     };
     int W = g->req_warps;
@@ -101,9 +116,9 @@ rmdec_status launch_grouped(rmdec_group* g, const rmdec_segment* segs, std::vect
     // Launches of at most one wave of that shape take the shape that minimises the busiest
     // CTA's work instead: frames go round-robin over the grid, so a CTA decodes at most
     // ceil(n_s / grid) frames of segment s, each in ceil(P / W) rounds of one decoder of that
-    // code. (Measured on four codes at 50-200 frames each: 0.084 against 0.112 ms; at two or
-    // more waves the CTAs that finish early speed up the busiest one, which this count
-    // ignores, and the default shape measured faster.)
+    // code. (Measured on four codes at 50 frames each: 0.072 against 0.113 ms in four
+    // launches; at two or more waves the CTAs that finish early speed up the busiest one,
+    // which this count ignores, and the default shape measured faster.)
     int64_t total_all = 0;
     for (int i : order) total_all += segs[i].n_frames;
     if (!g->req_warps && !g->req_ctas && total_all <= (int64_t)g->sm_count * occ_for(W)) {
