@@ -283,6 +283,9 @@ class Group:
         return outs
 
     def set_tuning(self, warps_per_cta=0, ctas_per_sm=0):
+        """Launch shape of the grouped launches: warps per CTA (1..20; 0 = the default, with
+        wide CTAs for launches of at most one wave) and a cap on CTAs per SM (0 = occupancy).
+        Never changes results."""
         self._check(self._lib.rmdec_group_set_tuning(self._h, warps_per_cta, ctas_per_sm))
 
     def set_split(self, min_frames_alone=0):
