@@ -8,10 +8,11 @@ The arithmetic lives in ``rm_oracle.c`` / ``pfht_core.inc`` (plain C, FP64 and i
 following Algorithms 2-5 and Eqs. (2)-(8) of the paper step by step); this module only
 compiles that file with gcc and marshals numpy arrays through ctypes.
 
-Parity status: every function here is pinned by ``tests/test_oracle_pins.py`` against
-closed forms, brute force and the paper's printed FER values. Unpinned: the exact
-complexity count C of the paper (its Table 1 cannot be reproduced, so ``ops`` is this
-oracle's own count).
+Parity status: every decoding function here is pinned by ``tests/test_oracle_pins.py``
+against closed forms, brute force and the paper's printed FER values. Parity unpinned: the
+operation count ``ops`` (the roofline numerator). The paper's own complexity count C (its
+Table 1) cannot be reproduced for L > 1, so ``ops`` is this oracle's counting convention,
+checked only for agreement with ``paper_2108_12550_gb300/opcount.py``.
 """
 from __future__ import annotations
 
