@@ -562,7 +562,7 @@ struct Decoder {
 
     // --------------------------------------------------- permutation selection ---
     // 2L candidates: candidate c permutes the LLRs of source path c mod L; its reliability
-    // LM_c = sum_{i < N_v/2} |f(tmp_i, tmp_{i+N_v/2})| (Algorithm 2, lines 6-11). For an
+    // LM_c = sum_{i < N_v/2} |f(tmp_i, tmp_{i+N_v/2})| (Algorithm 2, scoring of the candidates). For an
     // affine permutation, {pi(i), pi(i + N_v/2)} = {j, j ^ a} with a the image of the top
     // index bit, so LM_c = sum over the pairs {j, j ^ a} of min(|alpha_j|, |alpha_{j^a}|),
     // summed here with one representative j per pair (bit msb(a) clear). Returns, in lane
@@ -715,7 +715,7 @@ struct Decoder {
             }
             // this node's LLRs were just written with path l in slot l
             if (w.lane < L) ps.slot[S] = w.lane;
-            // f: left child RM(RR-1, S-1) (Algorithm 2, line 13)
+            // f: left child RM(RR-1, S-1) (Algorithm 2)
             if constexpr (ROOT) {
 #pragma unroll 1
                 for (int l = 0; l < L; l++) {
@@ -752,7 +752,7 @@ struct Decoder {
             }
             __syncwarp();
             node<RR - 1, S - 1, OFF, false, SPINE, (PEND | (1u << S))>(w, ps);
-            // g: right child RM(RR, S-1) from the path's own ancestor LLRs (line 15)
+            // g: right child RM(RR, S-1) from the path's own ancestor LLRs (Algorithm 2)
             if constexpr (ROOT) {
 #pragma unroll 1
                 for (int l = 0; l < L; l++) {
@@ -800,7 +800,7 @@ struct Decoder {
             }
             __syncwarp();
             node<RR, S - 1, OFF + H, false, false, PEND>(w, ps);
-            // combine x_v = (x_gamma ^ x_lambda, x_gamma) (line 17); the root does this for
+            // combine x_v = (x_gamma ^ x_lambda, x_gamma) (Algorithm 2); the root does this for
             // the winning path only
             if constexpr (!ROOT) {
                 if constexpr (H >= 32) {
@@ -823,7 +823,7 @@ struct Decoder {
                 }
                 __syncwarp();
                 if constexpr (PERM) {
-                    // undo pi*_l on the node's span (lines 18-19): x[pi(i)] = x'[i]
+                    // undo pi*_l on the node's span (Algorithm 2): x[pi(i)] = x'[i]
                     static_assert(OFF == 0, "permuted nodes lie on the left spine");
                     constexpr int SB = 1 << S;
                     if constexpr (SB >= 32) {
@@ -881,14 +881,14 @@ struct Decoder {
         }
         w.bsel = 0;
         node<R, M, 0, true, true, 0u>(w, ps);
-        // the list is sorted by metric: path 0 is the decoder's best (Algorithm 5, line 5)
+        // the list is sorted by metric: path 0 is the decoder's best (Algorithm 5)
         c0 = __shfl_sync(kFull, ps.rootc, 0);
         return __shfl_sync(kFull, ps.pm, 0);
     }
 
     // Root combine and un-permutation of path 0 into `dst` (the codeword in the channel
     // domain): x_root = (x_gamma ^ x_lambda, x_gamma), then x[sigma(i)] = x'[i] with
-    // sigma = pi^init o pi* the path's composed root permutation (Algorithm 2, lines 17-21),
+    // sigma = pi^init o pi* the path's composed root permutation (Algorithm 2),
     // read through the inverse map the host stores after the decoder's records.
     __device__ static void emit(Warp& w, int c0, uint32_t* dst) {
         uint32_t* b = bitbuf(w, w.bsel, 0);
