@@ -205,6 +205,55 @@ def perm_table(m: int, r: int, P: int, L: int, seed: int) -> np.ndarray:
     return tab
 
 
+def ga_record(cols, b: int = 0) -> np.ndarray:
+    """GA record [c_0 .. c_9, b] from the columns of A (c_t = A e_t) and the shift b."""
+    rec = np.zeros(PERM_REC, dtype=np.uint16)
+    rec[:len(cols)] = cols
+    rec[PERM_REC - 1] = b
+    return rec
+
+
+def selection_case(level: str, n_frames: int, seed: int, integer: bool = False):
+    """Frames and permutation records whose candidate reliabilities are ordered by
+    construction, for checks of the permutation selection with P = 1, L = 1.
+
+    Three GA(5) candidates: A and A2 map the top index bit to a = 16, B to a = 1 (A2 also maps
+    index bit 3 elsewhere than A, so the two split the next node differently). The frame
+    magnitudes are small on S = {0, 16, 5, 21} (closed under xor 16, disjoint from S xor 1)
+    and large elsewhere, so a left child pairing positions {j, j xor 16} meets the small
+    values two at a time and one pairing {j, j xor 1} meets them one at a time. level "root":
+    RM(2,5), the candidates act on the root; "deeper": RM(3,6) with identity root maps and a
+    large right half, the candidates act on the node RM(2,5). Signs are uniform. integer=True
+    gives integer magnitudes (1000-1160 and 1-3, right half 2000-2100). Returns
+    dict(m, r, head (records before the two candidates), A, A2, B, llr (F, 2^m) float64).
+    """
+    rng = np.random.default_rng(seed)
+    if level == "root":
+        m, r = 5, 2
+        head = [ga_record([1, 2, 4, 8, 16])]
+    elif level == "deeper":
+        m, r = 6, 3
+        i6 = ga_record([1, 2, 4, 8, 16, 32])
+        head = [i6, i6, i6]
+    else:
+        raise ValueError(level)
+    n = 1 << m
+    small = [0, 16, 5, 21]
+    if integer:  # 14 x 1000 + 2 x 1 > 12 x 1160 + 4 x 3: the order holds for every draw
+        mag = 1000.0 + rng.integers(0, 161, (n_frames, n))
+        mag[:, small] = 1.0 + rng.integers(0, 3, (n_frames, len(small)))
+        if level == "deeper":
+            mag[:, 32:] = 2000.0 + rng.integers(0, 101, (n_frames, 32))
+    else:
+        mag = 1.0 + 0.1 * rng.random((n_frames, n))
+        mag[:, small] = 0.01 * (1.0 + rng.random((n_frames, len(small))))
+        if level == "deeper":
+            mag[:, 32:] = 10.0 + rng.random((n_frames, 32))
+    llr = np.where(rng.random((n_frames, n)) < 0.5, -1.0, 1.0) * mag
+    return {"m": m, "r": r, "head": head, "A": ga_record([1, 2, 4, 8, 16]),
+            "A2": ga_record([1, 2, 8, 4, 16], b=6), "B": ga_record([16, 2, 4, 8, 1]), "llr": llr}
+
+
 SSC_STREAM = 0x53534300  # counter word 0 of the Aut-SSC permutation draws
 
 

@@ -64,6 +64,24 @@ def test_integer_llrs_bit_exact(m, r, P, L, eb, nf):
     assert np.array_equal(best2, ref["best"])
 
 
+@pytest.mark.parametrize("level", ["root", "deeper"])
+def test_constructed_permutation_selection_bit_exact(level):
+    """The oracle's selection pins on the GPU, which sums LM over the pairs {j, j xor a}
+    instead of gathering each candidate: the larger LM wins in either order, and on equal LM
+    the earlier candidate wins. Integer-valued LLRs (FP32), bit-exact against the oracle."""
+    c = I.selection_case(level, 700, seed=5, integer=True)
+    m, r = c["m"], c["r"]
+    y = c["llr"].astype(np.int64)
+    for c0, c1 in (("A", "B"), ("B", "A"), ("A", "A2"), ("A2", "A"), ("B", "B")):
+        tab = np.stack(c["head"] + [c[c0], c[c1]])[None]
+        ref = O.decode(m, r, 1, 1, tab, y, integer=True, want_margin=False)
+        dec = pkg.Decoder(m, r, 1, 1, dtype="f32", perms=tab)
+        info, cw, pm, best = _gpu_decode(dec, y.astype(np.float32))
+        assert np.array_equal(cw, ref["cw"]), (c0, c1)
+        assert np.array_equal(pm.astype(np.int64), ref["pm"]), (c0, c1)
+        assert np.array_equal(info, ref["info"]), (c0, c1)
+
+
 @pytest.mark.parametrize("m,r,P,L", [(7, 2, 8, 4), (9, 2, 4, 4)])
 def test_i16_llrs_bit_exact(m, r, P, L):
     fr = I.make_frames(m, r, 400, 2.0, seed=5)

@@ -1,7 +1,8 @@
 """Pins of the CPU oracle to facts fixed by the paper and by mathematics, independent of the
 oracle's own code: a library Hadamard matrix, closed-form FHT spectra, brute-force maximum
 likelihood on small codes, the path-metric = discrepancy identity, noiseless decoding, the
-integer mode, and the frame error rates printed in the paper's figures."""
+integer mode, the permutation selection on inputs whose reliability order is fixed by
+construction, and the frame error rates printed in the paper's figures."""
 import os
 
 import numpy as np
@@ -240,3 +241,37 @@ def test_fhtfscl_is_the_permuted_decoder_with_identity_permutations(m, r, L):
     q = I.quantize_i8(fr["llr"]).astype(np.int64)
     ai = O.decode_fhtfscl(m, r, L, q, integer=True)
     assert np.array_equal(ai["pm"], _disc(q, ai["cw"]).astype(np.int64))
+
+
+# ------------------------------------------- permutation selection (Algorithm 2) ---
+
+@pytest.mark.parametrize("level", ["root", "deeper"])
+@pytest.mark.parametrize("integer", [False, True])
+def test_selection_keeps_the_more_reliable_permutation_and_breaks_ties_by_index(level, integer):
+    """With L = 1 the path extension keeps the one of two candidate permutations whose left
+    child has the larger LM = sum |f| (Algorithm 2, the paper's 'maximum channel reliability'),
+    the earlier candidate on equal LM. For an affine map the left child pairs positions
+    {j, j xor a}, a the image of the top index bit, so LM depends on the map only through a,
+    and inputs.selection_case fixes its order by construction: LM(a = 16) = 14 large + 2 small
+    terms > LM(a = 1) = 12 large + 4 small terms (A and A2 share a = 16: equal LM). The decode
+    must then equal the decode whose two candidates are both the winner."""
+    c = I.selection_case(level, 1500, seed=11, integer=integer)
+    m, r, y = c["m"], c["r"], c["llr"]
+    if integer:
+        y = y.astype(np.int64)
+
+    def dec(c0, c1):
+        return O.decode(m, r, 1, 1, np.stack(c["head"] + [c0, c1])[None], y, integer=integer, want_margin=False)
+
+    def same(p, q):
+        return np.all(p["cw"] == q["cw"], axis=1) & (p["pm"] == q["pm"])
+
+    A, A2, B = c["A"], c["A2"], c["B"]
+    aa, bb, a2a2 = dec(A, A), dec(B, B), dec(A2, A2)
+    # larger LM wins, in either candidate order
+    assert np.all(same(dec(A, B), aa)) and np.all(same(dec(B, A), aa))
+    # equal LM: the earlier candidate wins
+    assert np.all(same(dec(A, A2), aa)) and np.all(same(dec(A2, A), a2a2))
+    # the checks have power: the three maps decide differently on many frames
+    assert np.mean(np.any(bb["cw"] != aa["cw"], axis=1)) > 0.2
+    assert np.mean(np.any(a2a2["cw"] != aa["cw"], axis=1)) > 0.2
