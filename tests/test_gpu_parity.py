@@ -82,6 +82,25 @@ def test_constructed_permutation_selection_bit_exact(level):
         assert np.array_equal(info, ref["info"]), (c0, c1)
 
 
+def test_tied_decoders_resolve_to_the_earliest_under_every_shape():
+    """Decoder 2 repeats decoder 0's table, so the two tie exactly on every frame; the winner
+    over decoders (Algorithm 5, strict <) must be the oracle's, never decoder 2, whether the two
+    run in different warps of a CTA or one after the other in the same warp."""
+    m, r, P, L = 7, 2, 4, 2
+    tab = I.perm_table(m, r, P, L, seed=23)
+    tab[2] = tab[0]
+    fr = I.make_frames(m, r, 800, 1.5, seed=41)
+    q = I.quantize_i8(fr["llr"])
+    ref = O.decode(m, r, P, L, tab, q.astype(np.int64), integer=True, want_margin=False)
+    assert len(set(ref["best"].tolist())) >= 3 and not np.any(ref["best"] == 2)
+    dec = pkg.Decoder(m, r, P, L, dtype="i8", perms=tab)
+    for w in (1, 2, 3, 4):
+        dec.set_tuning(w, 0)
+        info, cw, pm, best = _gpu_decode(dec, q)
+        assert np.array_equal(best, ref["best"]), w
+        assert np.array_equal(cw, ref["cw"]) and np.array_equal(pm.astype(np.int64), ref["pm"]), w
+
+
 @pytest.mark.parametrize("m,r,P,L", [(7, 2, 8, 4), (9, 2, 4, 4)])
 def test_i16_llrs_bit_exact(m, r, P, L):
     fr = I.make_frames(m, r, 400, 2.0, seed=5)

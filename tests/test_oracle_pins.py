@@ -275,3 +275,30 @@ def test_selection_keeps_the_more_reliable_permutation_and_breaks_ties_by_index(
     # the checks have power: the three maps decide differently on many frames
     assert np.mean(np.any(bb["cw"] != aa["cw"], axis=1)) > 0.2
     assert np.mean(np.any(a2a2["cw"] != aa["cw"], axis=1)) > 0.2
+
+
+# ----------------------------------------------------- best of P decoders (Algorithm 5) ---
+
+@pytest.mark.parametrize("integer", [False, True])
+def test_best_of_p_decoders_is_the_smallest_metric_earliest_on_ties(integer):
+    """The P decoders are independent (Algorithm 5): decoding with P tables must return, per
+    frame, the result of the decoder whose own run (P = 1, its table alone) has the smallest
+    path metric, the earliest such decoder on equal metrics. Decoder 2 repeats decoder 0's
+    table, so the two tie exactly on every frame and decoder 2 must never be chosen."""
+    m, r, P, L = 7, 2, 4, 2
+    tab = I.perm_table(m, r, P, L, seed=23)
+    tab[2] = tab[0]
+    fr = I.make_frames(m, r, 800, 1.5, seed=41)
+    y = I.quantize_i8(fr["llr"]).astype(np.int64) if integer else fr["llr"]
+    allp = O.decode(m, r, P, L, tab, y, integer=integer, want_margin=False)
+    alone = [O.decode(m, r, 1, L, tab[p:p + 1], y, integer=integer, want_margin=False) for p in range(P)]
+    pms = np.stack([a["pm"] for a in alone])          # (P, F)
+    want = np.argmin(pms, axis=0)                     # first index of the minimum
+    assert np.array_equal(allp["best"], want)
+    assert np.array_equal(allp["pm"], pms.min(axis=0))
+    for p in range(P):
+        sel = want == p
+        assert np.array_equal(allp["cw"][sel], alone[p]["cw"][sel])
+    assert not np.any(allp["best"] == 2)
+    # power: several decoders win somewhere, and decoder 0 (tied with 2) wins often
+    assert len(set(want.tolist())) >= 3 and np.mean(want == 0) > 0.2
