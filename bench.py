@@ -461,9 +461,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)  # before the process group, so NCCL binds each rank to its GPU
     if world > 1:
         dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
     m, r, P, L, ebn0, nf_default = wl
     nf = args.frames or nf_default
     n, k = I.rm_dims(m, r)
