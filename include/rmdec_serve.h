@@ -43,7 +43,8 @@ typedef struct {
 typedef struct {
     int64_t submitted, completed, frames_completed, batches;
     int64_t queued, in_flight;       /* requests waiting for admission / admitted, not done */
-    double latency_p50_us, latency_p99_us, latency_max_us;  /* over completed requests */
+    double latency_p50_us, latency_p99_us;  /* over the most recent 65,536 completed requests */
+    double latency_max_us;                   /* over all completed requests */
     double busy_seconds;             /* wall time from first submit to last completion */
     int64_t cancelled;               /* requests cancelled before admission */
 } rmdec_server_stats;
@@ -73,7 +74,8 @@ rmdec_status rmdec_server_poll(rmdec_server_t s, uint64_t request, int64_t timeo
  * (its batch completes normally), RMDEC_EINVAL for an unknown id. */
 rmdec_status rmdec_server_cancel(rmdec_server_t s, uint64_t request);
 
-/* Counters and latency percentiles over the requests completed so far. */
+/* Counters over the requests so far, and latency percentiles over the most recent 65,536
+ * completed requests (the server keeps a bounded record; the maximum covers all of them). */
 rmdec_status rmdec_server_stats_get(rmdec_server_t s, rmdec_server_stats *out);
 
 /* Stops the worker after draining in-flight batches, frees device memory. Queued requests

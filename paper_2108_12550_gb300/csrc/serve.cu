@@ -137,7 +137,12 @@ struct rmdec_server {
     bool stop = false;
     uint64_t next_id = 1;
     int64_t n_submitted = 0, n_completed = 0, frames_completed = 0, n_batches = 0, n_cancelled = 0;
+    // latencies of the most recent kLatWindow completed requests (a ring), and the maximum
+    // over all of them: the record stays bounded on a long-running server
+    static constexpr size_t kLatWindow = size_t(1) << 16;
     std::vector<double> latencies;
+    size_t lat_next = 0;
+    double lat_max = 0.0;
     bool have_first = false;
     Clock::time_point t_first, t_last;
     std::string err;
@@ -166,7 +171,13 @@ struct rmdec_server {
                 r->done = true;
                 r->t_done = now;
                 r->status = (e == cudaSuccess && !b->failed) ? RMDEC_OK : RMDEC_ECUDA;
-                latencies.push_back(std::chrono::duration<double, std::micro>(now - r->t_submit).count());
+                const double us = std::chrono::duration<double, std::micro>(now - r->t_submit).count();
+                if (latencies.size() < kLatWindow)
+                    latencies.push_back(us);
+                else
+                    latencies[lat_next] = us;
+                lat_next = (lat_next + 1) % kLatWindow;
+                lat_max = std::max(lat_max, us);
                 n_completed++;
                 frames_completed += r->frames;
             }
@@ -452,7 +463,7 @@ rmdec_status rmdec_server_cancel(rmdec_server_t s, uint64_t request) {
 
 rmdec_status rmdec_server_stats_get(rmdec_server_t s, rmdec_server_stats* out) {
     if (!s || !out) return RMDEC_EINVAL;
-    std::lock_guard<std::mutex> g(s->mu);
+    std::unique_lock<std::mutex> g(s->mu);
     memset(out, 0, sizeof *out);
     out->submitted = s->n_submitted;
     out->completed = s->n_completed;
@@ -463,16 +474,17 @@ rmdec_status rmdec_server_stats_get(rmdec_server_t s, rmdec_server_stats* out) {
     int64_t inf = 0;
     for (Batch* b : s->inflight) inf += (int64_t)b->reqs.size();
     out->in_flight = inf;
-    if (!s->latencies.empty()) {
-        std::vector<double> l = s->latencies;
+    if (s->have_first && s->n_completed)
+        out->busy_seconds = std::chrono::duration<double>(s->t_last - s->t_first).count();
+    std::vector<double> l = s->latencies;
+    out->latency_max_us = s->lat_max;
+    g.unlock();  // sort outside the lock: the worker keeps admitting and retiring meanwhile
+    if (!l.empty()) {
         std::sort(l.begin(), l.end());
         auto pct = [&](double q) { return l[std::min(l.size() - 1, (size_t)(q * (double)(l.size() - 1) + 0.5))]; };
         out->latency_p50_us = pct(0.50);
         out->latency_p99_us = pct(0.99);
-        out->latency_max_us = l.back();
     }
-    if (s->have_first && s->n_completed)
-        out->busy_seconds = std::chrono::duration<double>(s->t_last - s->t_first).count();
     return RMDEC_OK;
 }
 
