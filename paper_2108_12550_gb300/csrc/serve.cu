@@ -224,12 +224,33 @@ struct rmdec_server {
             return r->frames < c.wave;
         };
         const bool fused = fam >= 0 && families[fam].grp && small(pending.front());
-        // FIFO run of the oldest request's code (or, fused, of its family's small requests)
+        // FIFO run of the oldest request's code (or, fused, of its family's small requests),
+        // capped by max_batch_frames and by the whole arena: a batch larger than the arena
+        // could never be admitted, even with nothing in flight (the oldest request alone always
+        // fits, submit checks that)
         std::vector<Request*> take;
         int64_t frames = 0;
+        std::vector<std::pair<int, int64_t>> code_frames;  // per code, in order of first appearance
+        auto bytes_with = [&](const Request* r) {
+            size_t b = 0;
+            bool seen = false;
+            for (const auto& cf : code_frames) {
+                const int64_t f = cf.second + (cf.first == r->code ? r->frames : 0);
+                seen = seen || cf.first == r->code;
+                b += align256((size_t)f * codes[cf.first].in_bpf) + align256((size_t)f * codes[cf.first].out_bpf);
+            }
+            if (!seen)
+                b += align256((size_t)r->frames * codes[r->code].in_bpf) + align256((size_t)r->frames * codes[r->code].out_bpf);
+            return b;
+        };
         for (Request* r : pending) {
             if (fused ? (codes[r->code].family != fam || !small(r)) : r->code != code) continue;
-            if (frames + r->frames > cfg.max_batch_frames) break;
+            if (frames + r->frames > cfg.max_batch_frames || bytes_with(r) > (size_t)cfg.arena_bytes) break;
+            auto it = std::find_if(code_frames.begin(), code_frames.end(), [&](const auto& cf) { return cf.first == r->code; });
+            if (it == code_frames.end())
+                code_frames.emplace_back(r->code, r->frames);
+            else
+                it->second += r->frames;
             take.push_back(r);
             frames += r->frames;
         }

@@ -67,6 +67,34 @@ def test_mixed_requests_match_alone_decoding(fuse):
 
 
 @pytest.mark.gpu
+def test_batches_never_exceed_the_arena():
+    """Requests that fit the arena one at a time but not together (arena for one and a half,
+    batch cap for all three) are admitted in arena-sized batches instead of waiting for a
+    batch that could never fit. A slower request on the only stream makes the three queue
+    together before the first batch is formed."""
+    dec = pkg.Decoder(9, 2, 4, 4, perm_seed=2)
+    slow = pkg.Decoder(9, 3, 16, 8, perm_seed=3, dtype="f16")
+    one = 2048 * 512 * 4 + 2048 * 8  # LLRs and output words of one 2048-frame RM(2,9) request
+    srv = pkg.Server(n_streams=1, arena_bytes=one * 3 // 2, max_batch_frames=1 << 16)
+    cid, sid = srv.add_decoder(dec), srv.add_decoder(slow)
+    fs = I.make_frames(9, 3, 2048, 4.0, seed=5)
+    xs_slow = torch.from_numpy(I.to_f16(fs["llr"])).pin_memory()
+    out_slow = torch.zeros((2048, slow.kw), dtype=torch.int32).pin_memory()
+    fr = I.make_frames(9, 2, 2048, 3.0, seed=4)
+    xs = [torch.from_numpy(fr["llr"].astype(np.float32)).pin_memory() for _ in range(3)]
+    outs = [torch.zeros((2048, 2), dtype=torch.int32).pin_memory() for _ in range(3)]
+    rid_slow = srv.submit(sid, xs_slow, out_slow)
+    rids = [srv.submit(cid, x, o) for x, o in zip(xs, outs)]
+    for rid in [rid_slow] + rids:
+        assert srv.poll(rid, timeout_us=30_000_000)[0] == pkg.OK
+    ref = dec.decode(xs[0].cuda()).cpu()
+    assert all(torch.equal(o, ref) for o in outs)
+    assert torch.equal(out_slow, slow.decode(xs_slow.cuda()).cpu())
+    assert srv.stats()["batches"] == 4
+    srv.close()
+
+
+@pytest.mark.gpu
 def test_admission_waits_for_arena_memory_and_rejects_oversize():
     dec = pkg.Decoder(9, 2, 4, 4, perm_seed=2)
     # room for one 2048-frame batch of RM(2,9) FP32 LLRs (4 MiB + outputs)
