@@ -49,6 +49,17 @@ def test_encoder_matches_kronecker_matrix():
         assert np.array_equal(I.encode(u, m, r), (full @ _gm(m)) % 2)
 
 
+def test_kronecker_power_is_the_subset_matrix_and_an_involution():
+    """G^{(x)m} with G = [[1, 0], [1, 1]] has entry (i, j) = [j subset of i] (bits), and it is its
+    own inverse over GF(2): the encoder x = u G^{(x)m} and the decoders' u = x G^{(x)m} invert
+    each other."""
+    for m in range(1, 10):
+        g = _gm(m)
+        i, j = np.meshgrid(np.arange(1 << m), np.arange(1 << m), indexing="ij")
+        assert np.array_equal(g, ((i & j) == j).astype(g.dtype))
+        assert np.array_equal((g.astype(np.int64) @ g) % 2, np.eye(1 << m, dtype=np.int64))
+
+
 def test_rm25_minimum_distance_by_enumeration():
     m, r = 5, 2
     n, k = I.rm_dims(m, r)
