@@ -30,7 +30,9 @@ typedef struct rmdec_server *rmdec_server_t;
 typedef struct {
     int n_streams;            /* CUDA streams (batches in flight), 1..16 */
     int64_t arena_bytes;      /* device memory for resident request LLRs and outputs */
-    int64_t max_batch_frames; /* frames per batch cap (one kernel launch) */
+    int64_t max_batch_frames; /* frames per batch cap (one kernel launch); a batch is also kept
+                               * within arena_bytes, so requests that fit the arena only one at
+                               * a time are admitted one at a time */
     int64_t min_batch_frames; /* a batch waits up to max_wait_us for this many frames */
     int64_t max_wait_us;      /* longest time a request waits for batch companions */
     int fuse_codes;           /* 1: batch small requests (below one full wave of their code's own
