@@ -61,6 +61,8 @@ def _load():
             getattr(lib, name).restype = i
         lib.rmo_decode_fhtfscl.argtypes = [i, i, i, i, P, i64, i, P, P, P, P]
         lib.rmo_decode_fhtfscl.restype = i
+        lib.rmo_op_counts.argtypes = [i, i, i, i, i, P, P, i64, i, P, P]
+        lib.rmo_op_counts.restype = i
         lib.rmo_fht_f64.argtypes = [P, i]
         lib.rmo_fht_f64.restype = None
         _lib = lib
@@ -126,6 +128,24 @@ def decode_fhtfscl(m, r, L, llr, integer=False, n_threads=0):
     if rc != 0:
         raise RuntimeError(f"oracle FHT-FSCL decode failed rc={rc}")
     return {"cw": cw, "info": info, "pm": pm, "margin": margin}
+
+
+def op_counts(m, r, P, L, perms, llr, no_perm=False, n_threads=0):
+    """Both operation counts per frame of p-FHT-FSCL-L-P (or, with no_perm=True and P = 1,
+    FHT-FSCL-L): (ops, paper). ``ops`` is this build's count (the roofline numerator);
+    ``paper`` is the paper's complexity C by the rules of its Tables 1-2 (Section III-C)."""
+    lib = _load()
+    n = 1 << m
+    y = np.ascontiguousarray(llr, dtype=np.float64).reshape(-1, n)
+    F = y.shape[0]
+    ops = np.zeros(F, dtype=np.int64)
+    paper = np.zeros(F, dtype=np.int64)
+    tab = None if perms is None else np.ascontiguousarray(perms, dtype=np.uint16)
+    rc = lib.rmo_op_counts(m, r, P, L, 1 if no_perm else 0, _ptr(tab), _ptr(y), F, n_threads, _ptr(ops),
+                           _ptr(paper))
+    if rc != 0:
+        raise RuntimeError(f"oracle op_counts failed rc={rc}")
+    return ops, paper
 
 
 def aut_ssc(m, r, perms, llr, integer=False, n_threads=0):

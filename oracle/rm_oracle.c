@@ -95,6 +95,7 @@ typedef struct {
     int64_t *ops_out;
     int32_t *best_out;
     int bad; /* frames whose output is not a codeword (must stay 0) */
+    int64_t *paper_out; /* the paper's complexity count C per frame, or NULL */
 } job_t;
 
 static void *run_job(void *arg) {
@@ -112,12 +113,12 @@ static void *run_job(void *arg) {
             const double *y = (const double *)j->llr + f * N;
             best = decode_frame_f64(j->m, j->r, j->P, j->L, j->no_perm, j->perms, y, ba, bb, cw,
                                     (double *)j->pm_out + f, j->margin_out ? j->margin_out + f : NULL,
-                                    j->ops_out ? j->ops_out + f : NULL);
+                                    j->ops_out ? j->ops_out + f : NULL, j->paper_out ? j->paper_out + f : NULL);
         } else if (j->kind == 1) {
             const int64_t *y = (const int64_t *)j->llr + f * N;
             best = decode_frame_i64(j->m, j->r, j->P, j->L, j->no_perm, j->perms, y, ba, bb, cw,
                                     (int64_t *)j->pm_out + f, j->margin_out ? j->margin_out + f : NULL,
-                                    j->ops_out ? j->ops_out + f : NULL);
+                                    j->ops_out ? j->ops_out + f : NULL, j->paper_out ? j->paper_out + f : NULL);
         } else if (j->kind == 2) {
             best = aut_ssc_frame_f64(j->m, j->r, j->P, j->perms, (const double *)j->llr + f * N, cw,
                                      (double *)j->pm_out + f);
@@ -174,6 +175,21 @@ int rmo_decode_fhtfscl(int m, int r, int L, int integer, const void *llr, int64_
                        uint8_t *cw_out, uint8_t *info_out, void *pm_out, double *margin_out) {
     job_t j = {integer ? 1 : 0, m, r, 1, L, 1, NULL, llr, 0, 0, cw_out, info_out, pm_out, margin_out, NULL, NULL, 0};
     return run_batch(j, n_frames, n_threads);
+}
+
+/* Both operation counts of p-FHT-FSCL-L-P (no_perm = 0) or FHT-FSCL-L (no_perm = 1, P = 1,
+ * perms unused) on FP64 frames: ops_out [F] this build's count (the roofline numerator),
+ * paper_out [F] the paper's complexity C (Section III-C, Tables 1-2; see tally in
+ * pfht_core.inc). Either output may be NULL. */
+int rmo_op_counts(int m, int r, int P, int L, int no_perm, const uint16_t *perms, const double *llr,
+                  int64_t n_frames, int n_threads, int64_t *ops_out, int64_t *paper_out) {
+    if (no_perm && P != 1) return -1;
+    job_t j = {0, m, r, P, L, no_perm ? 1 : 0, perms, llr, 0, 0, NULL, NULL, NULL, NULL, ops_out, NULL, 0, paper_out};
+    double *pm = malloc(sizeof(double) * (n_frames > 0 ? n_frames : 1));
+    j.pm_out = pm;
+    int rc = run_batch(j, n_frames, n_threads);
+    free(pm);
+    return rc;
 }
 
 /* The same decoder in exact int64 arithmetic on integer LLRs (the quantised-LLR mode). */

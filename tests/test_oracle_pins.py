@@ -183,6 +183,70 @@ def test_ssc_baseline_properties():
     assert np.all(out["disc"] <= o4["disc"] + 1e-12)
 
 
+# ------------------------------------------- Aut-SSC node rules (repetition, Wagner SPC) ---
+
+def _ml_by_enumeration(llr, book):
+    """Smallest correlation discrepancy over an explicit list of codewords; returns the
+    index of the first minimiser per frame."""
+    disc = np.stack([_disc(llr, w[None, :].repeat(llr.shape[0], 0)) for w in book], axis=1)
+    return np.argmin(disc, axis=1), disc
+
+
+def _identity(m):
+    rec = np.zeros((1, I.PERM_REC), dtype=np.uint16)
+    rec[0, :m] = 1 << np.arange(m)
+    return rec
+
+
+@pytest.mark.parametrize("m", [3, 5, 8])
+def test_ssc_repetition_node_is_ml_on_the_repetition_code(m):
+    """RM(0, m) is the repetition code {0^N, 1^N}; SSC decodes it at one repetition node, whose
+    rule (the sign of the LLR sum, bit 0 on a zero sum) is ML. Enumerating both codewords pins
+    the rule, its sign convention and its tie rule (integer frames with zero sums)."""
+    n = 1 << m
+    book = np.stack([np.zeros(n, np.uint8), np.ones(n, np.uint8)])
+    fr = I.make_frames(m, 0, 400, -2.0, seed=50 + m)
+    out = O.aut_ssc(m, 0, _identity(m), fr["llr"])
+    idx, disc = _ml_by_enumeration(fr["llr"], book)
+    assert np.array_equal(out["cw"], book[idx])
+    np.testing.assert_allclose(out["disc"], disc.min(axis=1), rtol=0, atol=1e-9)
+    assert 0.05 < np.mean(idx == 1) < 0.95  # both codewords are chosen
+    # integer LLRs with exact zero sums: both words have equal discrepancy, bit 0 is chosen
+    rng = np.random.default_rng(m)
+    q = rng.integers(-3, 4, size=(300, n)).astype(np.int64)
+    q[:100, -1] -= q[:100].sum(axis=1)  # the first 100 frames sum to zero
+    outi = O.aut_ssc(m, 0, _identity(m), q, integer=True)
+    s = q.sum(axis=1)
+    assert np.array_equal(outi["cw"][:, 0], (s < 0).astype(np.uint8))
+    assert np.all(outi["cw"] == outi["cw"][:, :1])
+
+
+@pytest.mark.parametrize("m", [3, 4, 6])
+def test_ssc_wagner_node_is_ml_on_the_parity_check_code(m):
+    """RM(m-1, m) is the even-weight code; SSC decodes it at one SPC node, whose Wagner rule
+    (hard decisions, then flip the least reliable bit when the parity is odd) is ML.
+    Enumerating every even-weight word pins the rule: the least reliable bit, not another
+    one, and flipped only on odd parity."""
+    n = 1 << m
+    words = ((np.arange(1 << n)[:, None] >> np.arange(n)) & 1).astype(np.uint8) if n <= 16 else None
+    fr = I.make_frames(m, m - 1, 400, 0.0, seed=60 + m)
+    out = O.aut_ssc(m, m - 1, _identity(m), fr["llr"])
+    if words is not None:
+        book = words[np.sum(words, axis=1) % 2 == 0]
+        idx, disc = _ml_by_enumeration(fr["llr"], book)
+        assert np.array_equal(out["cw"], book[idx])
+    # any size: the chosen word has even weight and no even-weight word is closer; the
+    # best alternatives are the hard decision (odd parity fixed at one position) and, for an
+    # even hard decision, the hard decision itself
+    hd = (fr["llr"] < 0).astype(np.uint8)
+    assert np.all(np.sum(out["cw"], axis=1) % 2 == 0)
+    a = np.abs(fr["llr"])
+    odd = np.sum(hd, axis=1) % 2 == 1
+    best = np.where(odd, a.min(axis=1), 0.0)  # ML discrepancy of the even-weight code
+    np.testing.assert_allclose(out["disc"], best, rtol=0, atol=1e-12)
+    assert 0.2 < np.mean(odd) < 0.8
+
+
 def _paper_rows():
     rows = []
     for line in open(os.path.join(GOLD, "paper_fer.txt")):
@@ -210,6 +274,39 @@ def test_fer_matches_paper_figures(row):
     errs = int(np.sum(np.any(out["info"] != fr["u"], axis=1)))
     fer = errs / n_frames
     assert fer_paper / 2.2 <= fer <= fer_paper * 2.2, (fer, errs, n_frames, fer_paper)
+
+
+def _complexity_rows():
+    rows = []
+    for line in open(os.path.join(GOLD, "paper_complexity.txt")):
+        if line.strip() and not line.startswith("#"):
+            t = line.split()
+            rows.append((int(t[0]), int(t[1]), t[2], int(t[3]), int(t[4]), t[5], " ".join(t[6:])))
+    return rows
+
+
+@pytest.mark.parametrize("row", _complexity_rows(), ids=lambda r: r[6].replace(" ", "_"))
+def test_paper_complexity_count_reproduces_printed_values(row):
+    """The oracle's count in the paper's convention (floating-point additions and comparisons,
+    Section III-C) equals, to the digits printed, the complexity C that Fig. 5 prints for
+    FHT-FSCL-1 and p-FHT-FSC-1 on RM(2|3|4, 9) and that Table 5 prints for p-FHT-FSCL-1-M1 on
+    RM(2|3|4, 8) and RM(2, 9). Every term of the L = 1 count enters: f and g (one per
+    output), the FHT's s 2^s additions, the SPC node's 2^s, and each permuted node's 2L 2^(s-1)
+    reliability evaluations plus the 2L log2(2L) sort; C is P times the count of one decoder.
+    A dropped, doubled or misplaced term moves at least one of the ten values."""
+    m, r, dec, P, L, printed, _ = row
+    fr = I.make_frames(m, r, 2, 3.0, seed=17)
+    if dec == "fhtfscl":
+        ops, paper = O.op_counts(m, r, 1, L, None, fr["llr"], no_perm=True)
+    else:
+        ops, paper = O.op_counts(m, r, P, L, I.perm_table(m, r, P, L, seed=17), fr["llr"])
+    assert paper[0] == paper[1]  # the count depends on the code, not on the frame
+    mant = printed.upper().split("E")[0]
+    digits = len(mant.replace(".", "").lstrip("0"))
+    got = f"{float(paper[0]):.{digits - 1}E}"
+    assert float(got) == float(printed), (int(paper[0]), got, printed)
+    # this build's count (the roofline numerator) holds every term of the paper's count
+    assert np.all(ops > paper)
 
 
 @pytest.mark.parametrize("m,r,P,L", [(5, 2, 4, 2), (7, 2, 8, 4), (9, 2, 20, 4), (9, 3, 16, 8), (6, 3, 2, 1)])
