@@ -169,6 +169,32 @@ void rmdec_graph_destroy(rmdec_graph_t g);
  * exhausting a shared GPU; n = 0 disarms it. Process-wide. Not part of the paper's method. */
 rmdec_status rmdec_debug_fail_device_allocs(int64_t n);
 
+/* Decoding for callers that cannot allocate device memory. The paper has no counterpart:
+ * this entry point exists for deployments, not for the method. Some callers may not call
+ * cudaMalloc at decode time: code inside a framework whose caching allocator owns all device
+ * memory, real-time loops that fix their memory budget at start-up, or plug-ins loaded into a
+ * host process that forbids device allocations after initialisation. rmdec_decode allocates
+ * the handle's permutation and position tables on the device at its first call; this call
+ * instead uploads them, on `stream`, into one fixed device array that the library holds
+ * (128 KiB, present on every GPU that loads the library until the process exits) and runs
+ * the same decoder kernel. It calls no cudaMalloc, cudaFree or other allocating routine.
+ * Arguments, layouts and results are those of rmdec_decode (llr_dev and bits_out_dev are
+ * device buffers owned by the caller; llr_dev 16-byte aligned).
+ * Limits and rules:
+ *   - the decoder's tables must fit the array: per decoder 2 * (r-1) * 2L maps of 22 bytes for
+ *     p-FHT-FSCL (one map of 22 bytes per permutation for Aut-SSC), plus 2K bytes of
+ *     positions; larger configurations (e.g. RM(3,9) with P = 128, L = 8) return RMDEC_EINVAL
+ *     and launch nothing;
+ *   - the first call on each device looks up the array's device address (with that device
+ *     current); make that first call before any stream capture;
+ *   - every call shares the one array, which keeps the last call's tables: calls whose work
+ *     overlaps on the GPU (other streams, other threads, other handles) race and may decode
+ *     with another handle's tables. Issue them on one stream, or wait for the previous call.
+ *   - the handle's launch-shape request (rmdec_set_tuning) is honoured; diagnostics outputs
+ *     are not offered. */
+rmdec_status rmdec_decode_noalloc(rmdec_t h, const void *llr_dev, int64_t n_frames, uint32_t *bits_out_dev,
+                                  void *stream);
+
 /* Per-thread description of the last failure on this handle (or of the last failed create
  * when h is NULL). Never NULL; valid until the next call on the same handle. */
 const char *rmdec_last_error(rmdec_t h);

@@ -58,6 +58,7 @@ def load_library():
         "rmdec_decode": ([V, V, I64, V, V], I),
         "rmdec_decode_debug": ([V, V, I64, V, V, V, V, V], I),
         "rmdec_decode_host": ([V, V, I64, V, V], I),
+        "rmdec_decode_noalloc": ([V, V, I64, V, V], I),
         "rmdec_submit": ([V, V, I64, V, V, ctypes.POINTER(U64)], I),
         "rmdec_poll": ([V, U64, I64], I),
         "rmdec_last_error": ([V], ctypes.c_char_p),
@@ -172,6 +173,14 @@ class Decoder:
         F = llr.shape[0]
         out = self._alloc_bits(F, out)
         self._check(self._lib.rmdec_decode(self._h, _ptr(llr), F, _ptr(out), _stream_ptr(stream)))
+        return out
+
+    def decode_noalloc(self, llr, out, stream=None):
+        """rmdec_decode_noalloc: as decode, but the library allocates no device memory (its
+        tables go to a fixed device array shared by all such calls; see include/rmdec.h).
+        The caller supplies `out` (int32 CUDA tensor [F, ceil(k/32)])."""
+        self._check(self._lib.rmdec_decode_noalloc(self._h, _ptr(llr), llr.shape[0], _ptr(out),
+                                                   _stream_ptr(stream)))
         return out
 
     def decode_debug(self, llr, stream=None):

@@ -873,3 +873,145 @@ const char* rmdec_last_error(rmdec_t h) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------ decoding without allocation ---
+// rmdec_decode_noalloc reads the permutation maps and information positions from a table
+// that the library holds in a fixed device array, instead of from the handle's own
+// cudaMalloc'd tables, so that callers who must not allocate device memory can still decode.
+constexpr size_t kNoAllocTableBytes = 128 * 1024;  // tables of P decoders + K positions
+constexpr int kNoAllocMaxDevices = 64;
+
+// The device copy of the tables: one per GPU that loads the library, held until exit.
+static __device__ __align__(256) uint16_t g_noalloc_tables[kNoAllocTableBytes / 2];
+
+namespace {
+
+// The host image the tables are uploaded from. Every rmdec_decode_noalloc call overwrites
+// it and the device copy.
+uint16_t g_noalloc_host[kNoAllocTableBytes / 2];
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};  // device address of g_noalloc_tables per device
+
+// The layout device_records() builds (per decoder its maps, then their inverses), written
+// into a caller buffer of at least rec_words(h) elements.
+size_t noalloc_rec_words(const rmdec_ctx* h) {
+    if (h->algo == 1) return h->perms.size();
+    return (size_t)h->P * 2 * n_perm_levels(h->m, h->r) * 2 * h->L * kRec;
+}
+
+void noalloc_write_records(const rmdec_ctx* h, uint16_t* out) {
+    if (h->algo == 1) {
+        memcpy(out, h->perms.data(), h->perms.size() * sizeof(uint16_t));
+        return;
+    }
+    const int rpd = h->records_per_decoder(), nlev = n_perm_levels(h->m, h->r), L = h->L;
+    const size_t nrec = (size_t)nlev * 2 * L;
+    for (int p = 0; p < h->P; p++) {
+        const uint16_t* base = h->perms.data() + (size_t)p * rpd * kRec;
+        uint16_t* dst = out + (size_t)p * 2 * nrec * kRec;
+        for (int lev = 0; lev < nlev; lev++)
+            for (int c = 0; c < 2 * L; c++) {
+                const uint16_t* cand = base + (size_t)(L + lev * 2 * L + c) * kRec;
+                const size_t q = (size_t)lev * 2 * L + c;
+                uint16_t* o = dst + q * kRec;
+                if (lev == 0) compose(base + (size_t)(c % L) * kRec, cand, h->m, o);
+                else memcpy(o, cand, sizeof(uint16_t) * kRec);
+                invert(o, h->m - lev, dst + (nrec + q) * kRec);
+            }
+    }
+}
+
+}  // namespace
+
+extern "C" rmdec_status rmdec_decode_noalloc(rmdec_t h, const void* llr_dev, int64_t n_frames,
+                                             uint32_t* bits_out_dev, void* stream) {
+    if (!h) return RMDEC_EINVAL;
+    if (n_frames < 0) return h->fail(RMDEC_EINVAL, "n_frames < 0");
+    if (n_frames == 0) return RMDEC_OK;
+    if (!llr_dev || !bits_out_dev) return h->fail(RMDEC_EINVAL, "null llr or output pointer");
+    if (reinterpret_cast<uintptr_t>(llr_dev) % 16) return h->fail(RMDEC_EINVAL, "llr buffer must be 16-byte aligned");
+    const size_t rec_words = noalloc_rec_words(h);
+    const size_t info_off = (rec_words + 7) / 8 * 8;  // 16-byte aligned start of the positions
+    const size_t words = info_off + (size_t)h->k;
+    if (words * sizeof(uint16_t) > kNoAllocTableBytes)
+        return h->fail(RMDEC_EINVAL,
+                       "rmdec_decode_noalloc: this decoder's tables need %zu bytes, above the fixed %zu-byte "
+                       "table (use fewer decoders P or a smaller list size, or rmdec_decode)",
+                       words * sizeof(uint16_t), kNoAllocTableBytes);
+    cudaError_t e;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return h->fail(RMDEC_EDEVICE, "no CUDA device: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return h->fail(RMDEC_EDEVICE, "device %d beyond the supported %d", dev, kNoAllocMaxDevices);
+    rmdec_host::KernelEntry kern;
+    if (!lookup_kernel(h, &kern)) return h->fail(RMDEC_EINVAL, "no kernel for m=%d r=%d L=%d", h->m, h->r, h->L);
+    int sms = 0, max_optin = 0;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+        return h->cuda_fail(e, "cudaDeviceGetAttribute");
+    if ((e = cudaFuncSetAttribute(kern.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)) != cudaSuccess)
+        return h->cuda_fail(e, "cudaFuncSetAttribute");
+    // launch shape: the handle's requested one, else the default rule of rmdec_set_tuning
+    const int wmax = max_warps_per_cta(h);
+    auto smem_for = [&](int W) { return (size_t)kern.fixed_bytes(h->P, h->k, W) + 16 + (size_t)W * kern.warp_bytes; };
+    auto occ_for = [&](int W) {
+        int o = 0;
+        if (smem_for(W) > (size_t)max_optin) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern.fn, 32 * W, smem_for(W)) != cudaSuccess) return 0;
+        return o;
+    };
+    int W = std::max(0, std::min(wmax, h->req_warps));
+    if (!W) {
+        auto score = [&](int c) {
+            const int occ = occ_for(c);
+            const bool even = h->algo != 0 || h->P % c == 0;
+            const bool two_each = h->algo != 0 || h->P >= 2 * c;
+            return std::make_tuple(occ * c, even, two_each, occ >= 2, -c);
+        };
+        auto best = score(1);
+        W = 1;
+        for (int c = 2; c <= wmax; c++)
+            if (score(c) > best) {
+                best = score(c);
+                W = c;
+            }
+    }
+    const int occ = occ_for(W);
+    if (occ < 1) return h->fail(RMDEC_EINVAL, "kernel cannot be resident with %d warps per CTA", W);
+    const int per_sm = h->req_ctas ? std::min(h->req_ctas, occ) : occ;
+
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        // once per device, with that device current: the device address of the table (the
+        // array's name in host code is only a host-side stand-in for it)
+        void* p = nullptr;
+        if ((e = cudaGetSymbolAddress(&p, g_noalloc_tables)) != cudaSuccess) return h->cuda_fail(e, "cudaGetSymbolAddress");
+        g_noalloc_addr[dev] = p;
+    }
+    uint16_t* d_tab = static_cast<uint16_t*>(g_noalloc_addr[dev]);
+    noalloc_write_records(h, g_noalloc_host);
+    for (int i = 0; i < h->k; i++) g_noalloc_host[info_off + i] = (uint16_t)h->info[i];
+    // a pageable source: the call returns once the driver has taken the bytes, so the host
+    // image may be rewritten by the next call
+    if ((e = cudaMemcpyAsync(d_tab, g_noalloc_host, words * sizeof(uint16_t), cudaMemcpyHostToDevice,
+                             (cudaStream_t)stream)) != cudaSuccess)
+        return h->cuda_fail(e, "table upload");
+    rmdec_dev::LaunchArgs a;
+    a.llr = llr_dev;
+    a.dtype = (int)h->dtype;
+    a.qclamp = (float)((1 << (24 - h->m)) - 1);
+    a.n_frames = n_frames;
+    a.P = h->P;
+    a.recs = d_tab;
+    a.info = d_tab + info_off;
+    a.K = h->k;
+    a.info_out = bits_out_dev;
+    a.cw_out = nullptr;
+    a.pm_out = nullptr;
+    a.best_out = nullptr;
+    a.single_start = h->single_start ? 1 : 0;
+    const unsigned grid = (unsigned)std::min<int64_t>(n_frames, (int64_t)sms * per_sm);
+    void* args[] = {&a};
+    e = cudaLaunchKernel(kern.fn, dim3(grid), dim3(32 * W), args, smem_for(W), (cudaStream_t)stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "kernel launch");
+    return RMDEC_OK;
+}
