@@ -34,12 +34,12 @@ WORKLOADS = {
     "rm25_p4_l2": (5, 2, 4, 2, 3.0, 1 << 21),
     "rm39_p16_l8": (9, 3, 16, 8, 4.0, 1 << 16),
 }
-METRIC = "frames/s RM(2,9) P=20 L=4 at FER~1e-4 Eb/N0"
-# DRAM bytes per frame from the ncu capture summarised in profiles/pfht_kernel_rm29_p20_l4.md,
-# valid only for the kernel code it was taken on (kernel_fingerprint() prefix)
+METRIC = "frames/s RM(2,9) P=20 L=4 at FER~1e-4 Eb/N0; p50/p99 latency, mixed load"
+# DRAM bytes per frame of one ncu capture of pfht_kernel<9,2,4> (16,384 frames: 37,077,504 B
+# read + 1,212,672 B written), valid only for the kernel code it was taken on (the prefix of
+# kernel_fingerprint())
 TRAFFIC = {"rm29_p20_l4": {"bytes_per_frame": (37077504 + 1212672) / 16384, "kernel_code_sha256": "168da8f3e1f977a3"}}
-SMS = 152
-LANES_PER_SM = 128
+LANES_PER_SM = 128  # INT32/FP32 lanes per SM: one ALU operation per lane per clock
 
 
 def kernel_fingerprint():
@@ -158,51 +158,61 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
-def run_serving(args):
-    """Serving mix: Poisson arrivals of requests over 16 decoder configurations; the
-    continuous-batching server against a plain per-request launch on the same trace."""
-    import torch
+class ServingMix:
+    """The serving mix: Poisson arrivals (rate per second) of requests drawn uniformly over 16
+    decoder configurations (RM(2,7), RM(2,8), RM(2,9), RM(3,9) x P in {8, 20} x INT8/FP32 LLRs,
+    L = 4), each of 1-4096 frames (log-uniform) at an Eb/N0 drawn uniformly from 2-5 dB (four
+    1-dB buckets of pre-generated frames per code, pinned host memory)."""
 
-    import paper_2108_12550_gb300 as pkg
+    POOL = 4096
 
-    codes = [(m, r) for (m, r) in [(7, 2), (8, 2), (9, 2), (9, 3)]]
-    cfgs = [(m, r, P, 4, dt) for (m, r) in codes for P in (8, 20) for dt in ("i8", "f32")]
-    decs = [pkg.Decoder(m, r, P, L, perm_seed=1 + i, dtype=dt) for i, (m, r, P, L, dt) in enumerate(cfgs)]
-    rng = np.random.default_rng(7)
-    pool_frames = 4096
-    pools = {}  # (config, Eb/N0 bucket) -> pinned LLRs
-    for ci, (m, r, P, L, dt) in enumerate(cfgs):
-        for bi, eb in enumerate((2.0, 3.0, 4.0, 5.0)):
-            llr, _ = _frames(m, r, pool_frames, eb, seed=1000 + ci * 10 + bi, chunk=pool_frames)
-            x = I.quantize_i8(llr) if dt == "i8" else llr
-            pools[(ci, bi)] = torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
-    n_req = args.requests
-    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, n_req))
-    trace = []
-    for q in range(n_req):
-        ci = int(rng.integers(len(cfgs)))
-        nf = int(np.exp(rng.uniform(0.0, np.log(4096))))
-        bi = min(3, int(rng.uniform(2.0, 5.0) - 2.0))
-        off = int(rng.integers(0, pool_frames - nf + 1))
-        x = pools[(ci, bi)][off:off + nf]
-        out = torch.zeros((nf, decs[ci].kw), dtype=torch.int32).pin_memory()
-        trace.append((ci, x, out, float(arrivals[q])))
-    total_frames = sum(t[1].shape[0] for t in trace)
-    for ci, d in enumerate(decs):  # build device tables and grow staging to the largest request
-        d.decode_host(pools[(ci, 0)], torch.zeros((pool_frames, d.kw), dtype=torch.int32))
-    torch.cuda.synchronize()
+    def __init__(self, n_req, rate, seed=7):
+        import torch
 
-    def serve(fuse):
+        import paper_2108_12550_gb300 as pkg
+
+        codes = [(7, 2), (8, 2), (9, 2), (9, 3)]
+        self.cfgs = [(m, r, P, 4, dt) for (m, r) in codes for P in (8, 20) for dt in ("i8", "f32")]
+        self.decs = [pkg.Decoder(m, r, P, L, perm_seed=1 + i, dtype=dt) for i, (m, r, P, L, dt) in enumerate(self.cfgs)]
+        rng = np.random.default_rng(seed)
+        pools = {}  # (code, dtype, Eb/N0 bucket) -> pinned LLRs
+        for ci_code, (m, r) in enumerate(codes):
+            for bi, eb in enumerate((2.0, 3.0, 4.0, 5.0)):
+                llr, _ = _frames(m, r, self.POOL, eb, seed=1000 + ci_code * 10 + bi, chunk=self.POOL)
+                pools[(m, r, "f32", bi)] = torch.from_numpy(np.ascontiguousarray(llr)).pin_memory()
+                pools[(m, r, "i8", bi)] = torch.from_numpy(np.ascontiguousarray(I.quantize_i8(llr))).pin_memory()
+        self.pools = pools
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+        self.trace = []
+        for q in range(n_req):
+            ci = int(rng.integers(len(self.cfgs)))
+            m, r, _, _, dt = self.cfgs[ci]
+            nf = int(np.exp(rng.uniform(0.0, np.log(4096))))
+            bi = min(3, int(rng.uniform(2.0, 5.0) - 2.0))
+            off = int(rng.integers(0, self.POOL - nf + 1))
+            x = pools[(m, r, dt, bi)][off:off + nf]
+            out = torch.zeros((nf, self.decs[ci].kw), dtype=torch.int32).pin_memory()
+            self.trace.append((ci, x, out, float(arrivals[q])))
+        self.frames = sum(t[1].shape[0] for t in self.trace)
+        for ci, d in enumerate(self.decs):  # build device tables and grow staging to the largest request
+            m, r, _, _, dt = self.cfgs[ci]
+            d.decode_host(pools[(m, r, dt, 0)], torch.zeros((self.POOL, d.kw), dtype=torch.int32))
+        torch.cuda.synchronize()
+
+    def serve(self, fuse, streams=4):
         """Replays the trace through the continuous-batching server; fuse = one grouped launch
-        per batch over all codes (else one launch per code)."""
-        for t in trace:
+        per batch over all codes (else one launch per code). Returns (seconds, latencies in
+        microseconds, server stats, the results)."""
+        import paper_2108_12550_gb300 as pkg
+
+        for t in self.trace:
             t[2].zero_()
-        srv = pkg.Server(n_streams=args.streams, arena_bytes=2 << 30, max_batch_frames=1 << 15,
+        srv = pkg.Server(n_streams=streams, arena_bytes=2 << 30, max_batch_frames=1 << 15,
                          min_batch_frames=1024, max_wait_us=500, fuse_codes=fuse)
-        ids = [srv.add_decoder(d) for d in decs]
+        ids = [srv.add_decoder(d) for d in self.decs]
         t0 = time.perf_counter()
         rids = []
-        for ci, x, out, at in trace:
+        for ci, x, out, at in self.trace:
             while time.perf_counter() - t0 < at:
                 pass
             rids.append(srv.submit(ids[ci], x, out))
@@ -215,22 +225,65 @@ def run_serving(args):
         t_srv = time.perf_counter() - t0
         stats = srv.stats()
         srv.close()
-        return t_srv, lat, stats, [t[2].clone() for t in trace]
+        return t_srv, lat, stats, [t[2].clone() for t in self.trace]
+
+    def plain(self):
+        """The plain per-request form on the same trace: one synchronous host-to-host decode per
+        request, in arrival order. Returns (seconds, latencies in microseconds)."""
+        import torch
+
+        s = torch.cuda.current_stream()
+        t0 = time.perf_counter()
+        plat = []
+        for ci, x, out, at in self.trace:
+            while time.perf_counter() - t0 < at:
+                pass
+            self.decs[ci].decode_host(x, out, s)
+            plat.append((time.perf_counter() - t0 - at) * 1e6)
+        return time.perf_counter() - t0, plat
+
+
+def _pct(v):
+    return {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99))}
+
+
+def serving_leg(n_req, rate):
+    """The latency half of the headline metric: the serving mix at a fixed offered load, the
+    server (small requests of all codes fused into grouped launches) against the plain
+    per-request launch on the same trace."""
+    mix = ServingMix(n_req, rate)
+    mix.serve(True)  # warm-up: first grouped launches, host page-in of the trace
+    t_srv, lat, stats, served = mix.serve(True)
+    t_plain, plat = mix.plain()
+    same = all(a.equal(t[2]) for a, t in zip(served, mix.trace))
+    return {"workload": "serving_mix", "offered_requests_per_s": rate, "requests": n_req, "frames": mix.frames,
+            "server": {"frames_per_s": mix.frames / t_srv, "latency_us": _pct(lat), "batches": stats["batches"],
+                       "form": "continuous batching, small requests of all codes in grouped launches"},
+            "plain_per_request": {"frames_per_s": mix.frames / t_plain, "latency_us": _pct(plat),
+                                  "form": "one synchronous rmdec_decode_host per request"},
+            "results_identical_alone_and_in_mix": bool(same),
+            "mix": "RM(2,7), RM(2,8), RM(2,9), RM(3,9) x P in {8,20} x INT8/FP32, L=4, 1-4096 frames "
+                   "log-uniform, Eb/N0 2-5 dB, Poisson arrivals"}
+
+
+def run_serving(args):
+    """Serving mix: Poisson arrivals of requests over 16 decoder configurations; the
+    continuous-batching server against a plain per-request launch on the same trace."""
+    import torch
+
+    n_req = args.requests
+    mix = ServingMix(n_req, args.rate)
+    trace, total_frames = mix.trace, mix.frames
+
+    def serve(fuse):
+        return mix.serve(fuse, args.streams)
 
     serve(True)  # warm-up: first grouped launches, host page-in of the trace
     t_fused, lat_f, stats_f, served_f = serve(True)
     t_srv, lat, stats, served = serve(False)
 
     # plain per-request launch: one synchronous host-to-host decode per request, in order
-    s = torch.cuda.current_stream()
-    t0 = time.perf_counter()
-    plat = []
-    for ci, x, out, at in trace:
-        while time.perf_counter() - t0 < at:
-            pass
-        decs[ci].decode_host(x, out, s)
-        plat.append((time.perf_counter() - t0 - at) * 1e6)
-    t_plain = time.perf_counter() - t0
+    t_plain, plat = mix.plain()
     same = all(torch.equal(a, t[2]) and torch.equal(b, t[2]) for a, b, t in zip(served, served_f, trace))
     line = {
         "metric": "frames/s serving mix (Poisson arrivals, mixed RM codes, P in {8,20}, L=4, INT8/FP32)",
@@ -442,6 +495,8 @@ def main():
     ap.add_argument("--cpu-frames", type=int, default=1500, help="CPU-baseline sample size")
     ap.add_argument("--ref-frames", type=int, default=1000, help="frames per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=8000,
+                    help="requests of the serving-mix latency leg of the default run (0: skip)")
     args = ap.parse_args()
     if args.workload == "serving_mix":
         return run_serving(args)
@@ -510,7 +565,7 @@ def main():
     dec.decode_host(host_in, host_out, stream)
     barrier()
     e0 = time.perf_counter()
-    e_steps = max(1, min(args.steps, 5))
+    e_steps = args.steps
     for _ in range(e_steps):
         dec.decode_host(host_in, host_out, stream)
     barrier()
@@ -528,11 +583,21 @@ def main():
     torch.cuda.synchronize()
     per_frame_value = n1 / (p0.elapsed_time(p1) * 1e-3)
 
+    # roofline: the slower of the ALU side (algorithmic operations at one per lane per clock)
+    # and the HBM side (LLRs read once, information bits written once)
     pk, src = _peaks()
     sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
     ops = opcount.ops_per_frame(m, r, P, L)
-    peak_ops = SMS * LANES_PER_SM * sm_mhz * 1e6  # one ALU op per lane per clock
-    achieved = ops * nf / (ms * 1e-3)
+    peak_ops = sms * LANES_PER_SM * sm_mhz * 1e6
+    hbm_bw = float(pk.get("hbm_gbs", 6800.0)) * 1e9
+    bytes_frame = llr_np.nbytes / nf + dec.kw * 4
+    t_launch = ms * 1e-3
+    t_alu, t_hbm = ops * nf / peak_ops, bytes_frame * nf / hbm_bw
+    if t_alu >= t_hbm:
+        bound, achieved, peak, unit = "alu", ops * nf / t_launch / 1e12, peak_ops / 1e12, "Tops/s"
+    else:
+        bound, achieved, peak, unit = "hbm", bytes_frame * nf / t_launch / 1e9, hbm_bw / 1e9, "GB/s"
     traffic = None
     tr = TRAFFIC.get(args.workload)
     if tr and args.dtype == "f32" and kernel_fingerprint().startswith(tr["kernel_code_sha256"]):
@@ -548,10 +613,15 @@ def main():
                    "launch": dict(zip(("warps_per_cta", "ctas_per_sm"), dec.get_tuning()))},
         "info_gbit_s": value * k / 1e9,
         "fer_of_timed_batch": fer,
-        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-                     "frac": achieved / peak_ops, "traffic": traffic, "traffic_unit": "bytes per launch",
-                     "peak_source": f"{SMS} SMs x {LANES_PER_SM} lanes x {sm_mhz:.0f} MHz ({src} max SM clock)",
-                     "ops_per_frame": ops},
+        "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                     "frac": max(t_alu, t_hbm) / t_launch, "traffic": traffic, "traffic_unit": "bytes per launch",
+                     "ops_per_frame": ops, "bytes_per_frame": bytes_frame,
+                     "sides": {"alu": {"seconds": t_alu, "peak_tops": peak_ops / 1e12,
+                                       "peak_source": f"{sms} SMs x {LANES_PER_SM} lanes x {sm_mhz:.0f} MHz "
+                                                      f"({src} max SM clock)"},
+                               "hbm": {"seconds": t_hbm, "peak_gbs": hbm_bw / 1e9,
+                                       "peak_source": f"{src} copy bandwidth"}},
+                     "launch_seconds": t_launch},
         "e2e": {"value": e_value, "unit": "frames/s", "h2d_bytes_per_step": int(llr_np.nbytes),
                 "d2h_bytes_per_step": int(nf * dec.kw * 4)},
         "plain_per_frame": {"value": per_frame_value, "unit": "frames/s",
@@ -561,6 +631,8 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(m, r, P, L, ebn0, args.cpu_frames)
+    if rank == 0 and world == 1 and args.workload == "rm29_p20_l4" and args.serving_requests > 0:
+        line["serving"] = serving_leg(args.serving_requests, args.rate)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -50,9 +50,17 @@ typedef enum {
 } rmdec_dtype;
 
 /* Creates a p-FHT-FSCL-L-P decoder for RM(r, m) (Algorithm 5 with Algorithm 2 per decoder).
- * Supported: 4 <= m <= 9, r in {2, 3} with r <= m - 2 (the root is a permuted node,
- * 1 < r < m - 1), 1 <= P <= 128, L in {1, 2, 4, 8} (P = M_1 = 100, L = 1 is the paper's
- * p-FHT-FSCL-1-100).
+ * Supported, with 1 <= P <= 128:
+ *   - 4 <= m <= 10, r in {2, 3} with r <= m - 2 (the root is a permuted node, 1 < r < m - 1),
+ *     L in {1, 2, 4, 8} (P = M_1 = 100, L = 1 is the paper's p-FHT-FSCL-1-100);
+ *   - 2 <= m <= 10, r = 1 or r = m - 1, L in {1, 2, 4, 8, 16, 32}: the root is itself an FHTL
+ *     (RM(1, m), Algorithms 3-4) or SPCL (RM(m-1, m), Eqs. (2)-(6)) node. Algorithm 2 decodes
+ *     such a root before any permuted node and never undoes the initial permutations outside
+ *     the permuted branch; the permutations, automorphisms of the code, would only copy the
+ *     same candidate words into every path. Every decoder therefore decodes y with one live
+ *     path, which returns the maximum-likelihood word (largest |c_k|, ties to the smaller k;
+ *     or the hard decision with the least reliable bit fixing the parity), decoder 0 winning.
+ *     L and P do not change the result; the permutation table is kept but unused.
  * The affine permutations x -> Ax + b of GA(m) that Algorithm 2 draws (L initial ones and
  * 2L candidates at each of the r - 1 permuted nodes, per decoder) are sampled on the host
  * from perm_seed with Philox4x32-10 (counter (p, q, attempt, 'PERM'), key = perm_seed) and
@@ -78,7 +86,12 @@ rmdec_status rmdec_create_aut_ssc(rmdec_t *out, int m, int r, int P_ssc, uint64_
 /* Releases the handle and its device memory. Waits for the handle's outstanding work. */
 void rmdec_destroy(rmdec_t h);
 
-/* Sets the LLR element type read by the decode calls (default RMDEC_LLR_F32). */
+/* Sets the LLR element type read by the decode calls (default RMDEC_LLR_F32). The decoder's
+ * input is the vector of channel LLRs y = 2r/sigma^2 of a BPSK word over AWGN (Section II-A);
+ * the paper computes in floating point throughout. The narrower types are this library's
+ * storage formats for that vector, not part of the paper's method: F16 is widened to F32 on
+ * load; I8/I16 codes are decoded exactly in integer arithmetic (see rmdec_dtype). Takes
+ * effect on the next decode; an unknown type returns RMDEC_EINVAL. */
 rmdec_status rmdec_set_dtype(rmdec_t h, rmdec_dtype t);
 
 /* Number of uint16 permutation records the handle holds (11 uint16 per record:
@@ -88,12 +101,18 @@ rmdec_status rmdec_set_dtype(rmdec_t h, rmdec_dtype t);
  * Aut-SSC layout: P_ssc records of GA(m). */
 rmdec_status rmdec_perm_count(rmdec_t h, int64_t *n_records);
 /* Host copies in / out of the permutation table (n_records must equal rmdec_perm_count).
- * set_perms rejects records that are not invertible affine maps of the right size. */
+ * set_perms rejects records that are not invertible affine maps of the right size. New
+ * records reach the device at the next decode of the handle, which first waits for all work
+ * on the device (so that no queued decode reads a half-written table) and then overwrites the
+ * handle's device tables in place: graphs (rmdec_graph_create) and grouped launches that use
+ * the handle decode with the new permutations from then on. */
 rmdec_status rmdec_get_perms(rmdec_t h, uint16_t *perms_host, int64_t n_records);
 rmdec_status rmdec_set_perms(rmdec_t h, const uint16_t *perms_host, int64_t n_records);
 
-/* Code parameters: *n = N, *k = K, *info_idx = the K information positions
- * I = {i : popcount(i) >= m - r} in ascending order (owned by the handle). Any output
+/* Code parameters of RM(r, m) (Section II-A): *n = N = 2^m, *k = K = sum_{i<=r} C(m, i),
+ * *info_idx = the K information positions I = {i : popcount(i) >= m - r} in ascending order,
+ * i.e. the rows of G^{(x)m} of weight at least 2^(m-r) (owned by the handle, valid until
+ * rmdec_destroy). The decoded bits of every decode call are u_I in this order. Any output
  * pointer may be NULL. */
 rmdec_status rmdec_info(rmdec_t h, int *n, int *k, const int **info_idx);
 
@@ -101,7 +120,10 @@ rmdec_status rmdec_info(rmdec_t h, int *n, int *k, const int **info_idx);
  * stream). llr_dev: device, [n_frames][N] elements of the handle's dtype, row-major, 16-byte
  * aligned. bits_out_dev: device, [n_frames][ceil(K/32)] uint32, the decoded information bits
  * u_I in ascending order of I (u = x G^{(x)m} of the selected codeword x, Section II-A).
- * n_frames == 0 is a no-op. The first call on a handle uploads its tables (synchronous). */
+ * n_frames == 0 is a no-op. The first call on a handle uploads its tables (synchronous).
+ * LLRs are expected to be finite: a frame holding NaN or infinite values still yields a
+ * codeword of one of the decoders (which one is unspecified) and leaves the other frames of
+ * the batch unaffected. */
 rmdec_status rmdec_decode(rmdec_t h, const void *llr_dev, int64_t n_frames, uint32_t *bits_out_dev,
                           void *stream);
 
@@ -124,13 +146,17 @@ rmdec_status rmdec_decode_host(rmdec_t h, const void *llr_host, int64_t n_frames
 
 /* Asynchronous submission: enqueues rmdec_decode on `stream`, records a completion event and
  * returns a ticket (> 0). The caller keeps the buffers alive until rmdec_poll reports
- * completion. At most 1024 tickets may be outstanding per handle (RMDEC_EBUSY beyond). */
+ * completion. At most 1024 tickets may be outstanding per handle (RMDEC_EBUSY beyond).
+ * Not part of the paper's method (which decodes one received word at a time): an interface
+ * for callers that overlap decoding with other work; the decode itself is rmdec_decode's. */
 rmdec_status rmdec_submit(rmdec_t h, const void *llr_dev, int64_t n_frames, uint32_t *bits_out_dev,
                           void *stream, uint64_t *ticket);
 
 /* Waits up to timeout_us microseconds (0 = just check) for a ticket. Returns RMDEC_OK once
  * complete (the ticket is then retired), RMDEC_EBUSY if timeout_us == 0 and not complete,
- * RMDEC_ETIMEDOUT if the wait expired, RMDEC_EINVAL for an unknown ticket. */
+ * RMDEC_ETIMEDOUT if the wait expired, RMDEC_EINVAL for an unknown ticket. Host-side only
+ * (an event query, then sleeps of 20 us); no device code waits. Not part of the paper's
+ * method: the completion half of rmdec_submit. */
 rmdec_status rmdec_poll(rmdec_t h, uint64_t ticket, int64_t timeout_us);
 
 /* Launch shape: warps per CTA (1..20, at most P; Aut-SSC handles use at most 4; the decoders
@@ -155,7 +181,10 @@ rmdec_status rmdec_autotune(rmdec_t h, int64_t n_frames, const char *cache_path,
 /* A captured host-to-host decode pipeline for fixed buffers: copy n_frames LLRs from
  * llr_host, decode, copy the information bits to bits_out_host (layouts as in
  * rmdec_decode_host), recorded once as a CUDA graph and replayed with one launch. The graph
- * owns its device buffers; the host buffers must outlive it (pinned memory recommended). */
+ * owns its device buffers; the host buffers must outlive it (pinned memory recommended). The
+ * graph reads the handle's device tables at every replay: the handle must outlive the graph,
+ * and a replay after rmdec_set_perms (and a decode that uploads the new tables) decodes with
+ * the new permutations. The launch shape and LLR type are fixed at capture. */
 typedef struct rmdec_graph *rmdec_graph_t;
 rmdec_status rmdec_graph_create(rmdec_t h, const void *llr_host, int64_t n_frames, uint32_t *bits_out_host,
                                 rmdec_graph_t *out);

@@ -137,7 +137,7 @@ static void *run_job(void *arg) {
 
 static int run_batch(job_t proto, int64_t n_frames, int n_threads) {
     if (proto.m < 2 || proto.m > MAXM || proto.L < 1 || proto.L > 32 || proto.P < 1) return -1;
-    if (proto.kind <= 1 && !(2 <= proto.r && proto.r <= proto.m - 2)) return -1;
+    if (proto.kind <= 1 && !(1 <= proto.r && proto.r <= proto.m - 1)) return -1;
     if (proto.kind >= 2 && !(0 <= proto.r && proto.r <= proto.m)) return -1;
     if (n_threads <= 0) n_threads = (int)sysconf(_SC_NPROCESSORS_ONLN);
     if (n_threads > n_frames) n_threads = n_frames > 0 ? (int)n_frames : 1;

@@ -17,8 +17,8 @@ NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-
                      "--expt-relaxed-constexpr"]
 
 # slowest units first, so that they start first in the parallel build
-UNITS = (["group_l4.cu", "group_l2.cu", "group_l1.cu"] + [f"inst_m{m}.cu" for m in range(9, 3, -1)]
-         + ["rmdec_api.cu", "autssc.cu", "serve.cu", "group.cu"])
+UNITS = (["inst_m10.cu", "group_l4.cu", "group_l2.cu", "group_l1.cu"] + [f"inst_m{m}.cu" for m in range(9, 3, -1)]
+         + ["rmdec_api.cu", "autssc.cu", "mlroot.cu", "serve.cu", "group.cu"])
 HEADERS = ["pfht_kernel.cuh", "group_kernel.cuh", "rmdec_internal.h"]
 
 

@@ -222,12 +222,14 @@ __global__ void __launch_bounds__(256) autssc_kernel(LaunchArgs args) {
         if (warp == 0) {
             float bd = __int_as_float(0x7f800000);
             int bw = 0, bq = 1 << 30;
-            for (int q = 0; q < W; q++)
-                if (s_redq[q] >= 0 && (s_red[q] < bd || (s_red[q] == bd && s_redq[q] < bq))) {
-                    bd = s_red[q];
+            for (int q = 0; q < W; q++) {
+                const float v = s_red[q] == s_red[q] ? s_red[q] : __int_as_float(0x7f800000);  // NaN: last
+                if (s_redq[q] >= 0 && (v < bd || (v == bd && s_redq[q] < bq))) {
+                    bd = v;
                     bq = s_redq[q];
                     bw = q;
                 }
+            }
             const uint32_t* cw = reinterpret_cast<const uint32_t*>(wbase + bw * C::WARP_BYTES + C::OFF_BEST);
             if (args.cw_out)
                 for (int wd = lane; wd < NW; wd += 32) args.cw_out[f * NW + wd] = cw[wd];

@@ -213,6 +213,10 @@ rmdec_status rmdec_group_create(rmdec_group_t* out, const rmdec_t* decoders, int
             g_group_create_error = "decoder " + std::to_string(i) + " is not a p-FHT-FSCL decoder";
             return RMDEC_EINVAL;
         }
+        if (mi.m > 9) {
+            g_group_create_error = "decoder " + std::to_string(i) + ": codes longer than 512 are not supported in groups";
+            return RMDEC_EINVAL;
+        }
         if (!group_fn(mi.L)) {
             g_group_create_error = "decoder " + std::to_string(i) + ": list size " + std::to_string(mi.L) +
                                    " is not supported in groups (L in {1, 2, 4})";

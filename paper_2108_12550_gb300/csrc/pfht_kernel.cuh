@@ -1043,7 +1043,7 @@ __device__ __forceinline__ void decode_frame(const FrameJob& j, const FrameSmem&
         float bp = __int_as_float(0x7f800000);
         int bw = 0, bpp = 1 << 30;
         for (int q = 0; q < W; q++) {
-            const float v = s_redpm[q];
+            const float v = s_redpm[q] == s_redpm[q] ? s_redpm[q] : __int_as_float(0x7f800000);  // NaN: last
             const int pq = s_redp[q];
             if (pq >= 0 && (v < bp || (v == bp && pq < bpp))) {
                 bp = v;

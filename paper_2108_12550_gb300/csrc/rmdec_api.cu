@@ -147,7 +147,7 @@ std::atomic<int64_t> g_failing_allocs{0};  // device allocations still to fail (
 }  // namespace
 
 struct rmdec_ctx {
-    int algo = 0;  // 0: p-FHT-FSCL-L-P, 1: Aut-SSC-P
+    int algo = 0;  // 0: p-FHT-FSCL-L-P, 1: Aut-SSC-P, 2: p-FHT-FSCL of RM(1, m) or RM(m-1, m)
     bool single_start = false;  // FHT-FSCL: identity permutations, one live initial path
     int m = 0, r = 0, P = 0, L = 1, n = 0, k = 0;
     rmdec_dtype dtype = RMDEC_LLR_F32;
@@ -187,8 +187,8 @@ struct rmdec_ctx {
     rmdec_status cuda_fail(cudaError_t e, const char* what) {
         return fail(RMDEC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
     }
-    int records_per_decoder() const { return algo == 0 ? L + n_perm_levels(m, r) * 2 * L : 1; }
-    int64_t n_records() const { return algo == 0 ? (int64_t)P * records_per_decoder() : P; }
+    int records_per_decoder() const { return algo != 1 ? L + n_perm_levels(m, r) * 2 * L : 1; }
+    int64_t n_records() const { return algo != 1 ? (int64_t)P * records_per_decoder() : P; }
     int record_size(int q) const {  // GA(s) of record q within a decoder
         if (algo == 1 || q < L) return m;
         return m - (q - L) / (2 * L);
@@ -210,6 +210,7 @@ size_t llr_elem_bytes(rmdec_dtype t) {
 bool lookup_kernel(rmdec_ctx* h, rmdec_host::KernelEntry* e) {
     using namespace rmdec_host;
     if (h->algo == 1) return lookup_autssc(h->m, h->r, e);
+    if (h->algo == 2) return lookup_mlroot(h->m, h->r, e);
     switch (h->m) {
         case 4: return lookup_pfht_m4(h->r, h->L, e);
         case 5: return lookup_pfht_m5(h->r, h->L, e);
@@ -217,6 +218,7 @@ bool lookup_kernel(rmdec_ctx* h, rmdec_host::KernelEntry* e) {
         case 7: return lookup_pfht_m7(h->r, h->L, e);
         case 8: return lookup_pfht_m8(h->r, h->L, e);
         case 9: return lookup_pfht_m9(h->r, h->L, e);
+        case 10: return lookup_pfht_m10(h->r, h->L, e);
     }
     return false;
 }
@@ -257,12 +259,19 @@ rmdec_status ensure_device(rmdec_ctx* h) {
     if ((e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return h->cuda_fail(e, "cudaDeviceGetAttribute");
     std::vector<uint16_t> recs = device_records(h);
-    if (h->d_recs) cudaFree(h->d_recs);
-    if (h->d_info) cudaFree(h->d_info);
-    h->d_recs = nullptr;
-    h->d_info = nullptr;
-    if ((e = rmdec_host::device_alloc(reinterpret_cast<void**>(&h->d_recs), std::max<size_t>(recs.size(), 1) * 2)) != cudaSuccess) return h->fail(RMDEC_ENOMEM, "cudaMalloc records: %s", cudaGetErrorString(e));
-    if ((e = rmdec_host::device_alloc(reinterpret_cast<void**>(&h->d_info), std::max<size_t>(h->info.size(), 1) * 2)) != cudaSuccess) return h->fail(RMDEC_ENOMEM, "cudaMalloc info: %s", cudaGetErrorString(e));
+    if (h->d_recs && h->d_info && h->device == dev) {
+        // The table sizes are fixed per handle, so new permutations (rmdec_set_perms) go into
+        // the existing buffers: pointers that captured graphs and grouped launches hold stay
+        // valid and read the new tables. Wait until every queued use of the old ones is done.
+        if ((e = cudaDeviceSynchronize()) != cudaSuccess) return h->cuda_fail(e, "synchronize before table update");
+    } else {
+        if (h->d_recs) cudaFree(h->d_recs);
+        if (h->d_info) cudaFree(h->d_info);
+        h->d_recs = nullptr;
+        h->d_info = nullptr;
+        if ((e = rmdec_host::device_alloc(reinterpret_cast<void**>(&h->d_recs), std::max<size_t>(recs.size(), 1) * 2)) != cudaSuccess) return h->fail(RMDEC_ENOMEM, "cudaMalloc records: %s", cudaGetErrorString(e));
+        if ((e = rmdec_host::device_alloc(reinterpret_cast<void**>(&h->d_info), std::max<size_t>(h->info.size(), 1) * 2)) != cudaSuccess) return h->fail(RMDEC_ENOMEM, "cudaMalloc info: %s", cudaGetErrorString(e));
+    }
     std::vector<uint16_t> info16(h->info.begin(), h->info.end());
     if ((e = cudaMemcpy(h->d_recs, recs.data(), recs.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess) return h->cuda_fail(e, "upload records");
     if ((e = cudaMemcpy(h->d_info, info16.data(), info16.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess) return h->cuda_fail(e, "upload info");
@@ -274,7 +283,10 @@ rmdec_status ensure_device(rmdec_ctx* h) {
 
 // Widest CTA a handle's kernel accepts: pfht_kernel is built for up to kMaxWarps warps, and
 // more warps than decoders would idle.
-int max_warps_per_cta(const rmdec_ctx* h) { return h->algo == 0 ? std::min(h->P, rmdec_dev::kMaxWarps) : 4; }
+int max_warps_per_cta(const rmdec_ctx* h) {
+    if (h->algo == 2) return 8;  // one frame per warp
+    return h->algo == 0 ? std::min(h->P, rmdec_dev::kMaxWarps) : 4;
+}
 
 // Launch shape: warps per CTA (decoders of a frame split across warps) and resident CTAs.
 rmdec_status configure_shape(rmdec_ctx* h) {
@@ -385,9 +397,12 @@ rmdec_status launch(rmdec_ctx* h, const void* llr, int64_t n_frames, uint32_t* b
     a.best_out = best;
     a.single_start = h->single_start ? 1 : 0;
     const int64_t cap = (int64_t)h->sm_count * per_sm;
-    const unsigned grid = (unsigned)std::min<int64_t>(n_frames, cap);
+    // p-FHT-FSCL and Aut-SSC CTAs take one frame at a time; the first-order/parity-check root
+    // kernel decodes one frame per warp
+    const int64_t want = h->algo == 2 ? (n_frames + W - 1) / W : n_frames;
+    const unsigned grid = (unsigned)std::min<int64_t>(want, cap);
     void* args[] = {&a};
-    nvtxRangePushA(h->algo == 0 ? "rmdec_decode pfht" : "rmdec_decode aut-ssc");
+    nvtxRangePushA(h->algo == 1 ? "rmdec_decode aut-ssc" : "rmdec_decode pfht");
     cudaError_t e = cudaLaunchKernel(h->kern.fn, dim3(grid), dim3(32 * W), args, smem, stream);
     nvtxRangePop();
     if (e != cudaSuccess) return h->cuda_fail(e, "kernel launch");
@@ -400,9 +415,14 @@ rmdec_status make_handle(rmdec_t* out, int algo, int m, int r, int P, int L, uin
         return RMDEC_EINVAL;
     }
     *out = nullptr;
+    bool ml_root = false;  // RM(1, m) or RM(m-1, m): the root is an FHTL or SPCL node
     if (algo == 0) {
-        if (m < 4 || m > 9 || r < 2 || r > 3 || r > m - 2 || P < 1 || P > 128 || !(L == 1 || L == 2 || L == 4 || L == 8)) {
-            g_create_error = "unsupported p-FHT-FSCL configuration (need 4<=m<=9, r in {2,3}, r<=m-2, 1<=P<=128, L in {1,2,4,8})";
+        ml_root = m >= 2 && m <= 10 && (r == 1 || r == m - 1);
+        const bool pl_ok = P >= 1 && P <= 128 && L >= 1 && L <= (ml_root ? 32 : 8) && (L & (L - 1)) == 0;
+        const bool code_ok = ml_root || (m >= 4 && m <= 10 && r >= 2 && r <= 3 && r <= m - 2);
+        if (!code_ok || !pl_ok) {
+            g_create_error = "unsupported p-FHT-FSCL configuration (need 1<=P<=128 and either 4<=m<=10, r in {2,3}, "
+                             "r<=m-2, L in {1,2,4,8}, or 2<=m<=10, r in {1,m-1}, L in {1,2,4,8,16,32})";
             return RMDEC_EINVAL;
         }
     } else {
@@ -416,7 +436,7 @@ rmdec_status make_handle(rmdec_t* out, int algo, int m, int r, int P, int L, uin
         g_create_error = "host allocation failed";
         return RMDEC_ENOMEM;
     }
-    h->algo = algo;
+    h->algo = ml_root ? 2 : algo;
     h->m = m;
     h->r = r;
     h->P = P;
@@ -426,7 +446,7 @@ rmdec_status make_handle(rmdec_t* out, int algo, int m, int r, int P, int L, uin
         if (__builtin_popcount((unsigned)i) >= m - r) h->info.push_back(i);
     h->k = (int)h->info.size();
     h->perms.assign((size_t)h->n_records() * kRec, 0);
-    if (algo == 0) {
+    if (h->algo != 1) {
         const int rpd = h->records_per_decoder();
         for (int p = 0; p < P; p++)
             for (int q = 0; q < rpd; q++)

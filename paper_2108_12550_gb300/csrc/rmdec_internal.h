@@ -34,13 +34,17 @@ bool lookup_pfht_m6(int r, int L, KernelEntry* e);
 bool lookup_pfht_m7(int r, int L, KernelEntry* e);
 bool lookup_pfht_m8(int r, int L, KernelEntry* e);
 bool lookup_pfht_m9(int r, int L, KernelEntry* e);
+bool lookup_pfht_m10(int r, int L, KernelEntry* e);
 
 // Aut-SSC baseline kernels (autssc.cu).
 bool lookup_autssc(int m, int r, KernelEntry* e);
 
+// p-FHT-FSCL of RM(1, m) and RM(m-1, m), whose root is an FHTL or SPCL node (mlroot.cu).
+bool lookup_mlroot(int m, int r, KernelEntry* e);
+
 // What a grouped launch needs to know about one decoder handle.
 struct MemberInfo {
-    int algo = 0;  // 0: p-FHT-FSCL (and FHT-FSCL), 1: Aut-SSC
+    int algo = 0;  // 0: p-FHT-FSCL (and FHT-FSCL), 1: Aut-SSC, 2: RM(1, m) / RM(m-1, m) roots
     int m = 0, r = 0, L = 0, P = 0, n = 0, k = 0;
     int single = 0;
     int dtype = 0;

@@ -42,6 +42,10 @@ CONFIGS = [  # (m, r, P, L, Eb/N0, frames)
     (8, 2, 8, 4, 2.5, 600),
     (9, 2, 20, 4, 2.25, 333),    # RM(2,9), P=20, L=4 (ragged frame count)
     (9, 3, 16, 8, 4.0, 150),     # RM(3,9), P=16, L=8
+    (10, 2, 3, 4, 2.0, 120),     # RM(2,10) (length 1024)
+    (10, 2, 2, 8, 2.0, 60),
+    (10, 3, 2, 2, 3.0, 90),      # RM(3,10), two permuted levels
+    (10, 3, 1, 8, 3.0, 40),
 ]
 
 
@@ -216,9 +220,10 @@ def test_host_entry_point_and_tickets():
         dec.poll(t, 0)  # retired ticket
 
 
-@pytest.mark.parametrize("m,r,Ps", [(7, 2, 32), (9, 2, 64), (6, 3, 16)])
+@pytest.mark.parametrize("m,r,Ps", [(7, 2, 32), (9, 2, 64), (6, 3, 16), (9, 2, 512)])
 def test_aut_ssc_bit_exact(m, r, Ps):
-    fr = I.make_frames(m, r, 400, 2.0, seed=41)
+    # (9, 2, 512) is the size of the paper's Aut-SSC-512 comparison on RM(2,9)
+    fr = I.make_frames(m, r, 300 if Ps > 64 else 400, 2.0, seed=41)
     q = I.quantize_i8(fr["llr"])
     perms = I.ssc_perm_table(m, Ps, seed=6)
     ref = O.aut_ssc(m, r, perms, q.astype(np.int64), integer=True)
@@ -247,3 +252,52 @@ def test_p100_l1_bit_exact():
     dec = pkg.Decoder(m, r, P, L, dtype="i8", perms=perms)
     info, cw, pm, best = _gpu_decode(dec, q)
     assert np.array_equal(cw, ref["cw"]) and np.array_equal(best, ref["best"])
+
+
+@pytest.mark.parametrize("algo", ["pfht", "autssc"])
+def test_non_finite_llrs_give_in_range_results_and_leave_other_frames_alone(algo):
+    """Frames holding NaN or infinite LLRs have no meaningful decision, but they must still
+    return one of the decoders' codewords with an in-range winner index, and the other frames
+    of the batch must decode exactly as without them."""
+    m, r, P, L = 7, 2, 8, 4
+    fr = I.make_frames(m, r, 64, 2.0, seed=71)
+    x = fr["llr"].astype(np.float32)
+    dec = pkg.Decoder(m, r, P, L, perm_seed=3, algo=algo)
+    ref_info, ref_cw, ref_pm, ref_best = _gpu_decode(dec, x)
+    bad = x.copy()
+    bad[5, :] = np.nan
+    bad[9, 3] = np.inf
+    bad[12, :] = np.inf
+    bad[12, ::2] = -np.inf
+    bad[20, 7] = np.nan
+    info, cw, pm, best = _gpu_decode(dec, bad)
+    hit = [5, 9, 12, 20]
+    assert np.all((best >= 0) & (best < P))
+    for f in hit:  # a codeword of RM(2,7): its information bits re-encode to it
+        assert np.array_equal(I.encode(info[f:f + 1], m, r)[0], cw[f])
+    keep = np.setdiff1d(np.arange(64), hit)
+    assert np.array_equal(cw[keep], ref_cw[keep]) and np.array_equal(best[keep], ref_best[keep])
+
+
+@pytest.mark.parametrize("m,r", [(2, 1), (3, 1), (5, 1), (7, 1), (9, 1), (10, 1), (3, 2), (4, 3), (6, 5), (9, 8),
+                                 (10, 9)])
+@pytest.mark.parametrize("P,L", [(1, 1), (3, 16)])
+def test_first_order_and_parity_check_roots_match_the_oracle(m, r, P, L):
+    """RM(1, m) and RM(m-1, m), whose root is an FHTL or SPCL node: INT8 codes bit-exact
+    against the integer oracle (word, metric, winner; ties are frequent on the coarse codes),
+    FP32 LLRs to the same words with metrics within 1e-5 relative."""
+    fr = I.make_frames(m, r, 333, 1.0, seed=90 + m)
+    perms = I.perm_table(m, r, P, L, seed=5)
+    q = I.quantize_i8(fr["llr"] * 0.5)
+    ref = O.decode(m, r, P, L, perms, q.astype(np.int64), integer=True, want_margin=False)
+    dec = pkg.Decoder(m, r, P, L, dtype="i8", perms=perms)
+    info, cw, pm, best = _gpu_decode(dec, q)
+    assert np.array_equal(info, ref["info"]) and np.array_equal(cw, ref["cw"])
+    assert np.array_equal(pm.astype(np.int64), ref["pm"]) and np.array_equal(best, ref["best"])
+    ref = O.decode(m, r, P, L, perms, fr["llr"])
+    dec.set_dtype("f32")
+    info, cw, pm, best = _gpu_decode(dec, fr["llr"].astype(np.float32))
+    diff = np.any(cw != ref["cw"], axis=1)
+    assert np.all(ref["margin"][diff] < 1e-5)  # only FP32 near-ties may decide otherwise
+    np.testing.assert_allclose(pm[~diff], ref["pm"][~diff], rtol=1e-5, atol=1e-5 * np.mean(np.abs(fr["llr"])))
+

@@ -183,6 +183,54 @@ def test_ssc_baseline_properties():
     assert np.all(out["disc"] <= o4["disc"] + 1e-12)
 
 
+# ------------------------------- roots that are themselves FHTL / SPCL nodes (Algorithm 2) ---
+
+@pytest.mark.parametrize("m", [2, 3, 5, 7, 9])
+@pytest.mark.parametrize("integer", [False, True])
+def test_first_order_root_decodes_to_ml_by_enumeration(m, integer):
+    """RM(1, m) as a whole code: the root is an FHTL node, so every decoder returns the ML
+    word (largest |c_k|, ties to the smaller k, the sign of c_k); enumerating all 2^(m+1)
+    codewords in the order (k, sign) and taking the first of smallest discrepancy pins it,
+    including the tie rule on integer frames, where ties are frequent."""
+    r, P, L = 1, 3, 2
+    n = 1 << m
+    j = np.arange(n)
+    book = np.array([[(bin(k & v).count("1") & 1) ^ sgn for v in j] for k in range(n) for sgn in (0, 1)],
+                    dtype=np.uint8)
+    fr = I.make_frames(m, r, 300, 0.0, seed=70 + m)
+    y = I.quantize_i8(fr["llr"] * 0.3).astype(np.int64) if integer else fr["llr"]
+    out = O.decode(m, r, P, L, I.perm_table(m, r, P, L, seed=3), y, integer=integer, want_margin=False)
+    disc = np.stack([_disc(y, np.broadcast_to(w, y.shape)) for w in book], axis=1)
+    assert np.array_equal(out["cw"], book[np.argmin(disc, axis=1)])
+    assert np.array_equal(out["pm"], disc.min(axis=1)) if integer else np.allclose(out["pm"], disc.min(axis=1))
+    assert np.all(out["best"] == 0)  # every decoder decides alike: the first wins
+    if integer:
+        assert np.mean(np.sum(disc == disc.min(axis=1, keepdims=True), axis=1) > 1) > 0.05  # ties occur
+
+
+@pytest.mark.parametrize("m", [3, 4, 6, 10])
+def test_parity_check_root_decodes_by_wagner_rule(m):
+    """RM(m-1, m): the root is an SPCL node; the best path is the hard decision with the least
+    reliable bit flipped on odd parity, which is ML (pinned by enumerating the even-weight
+    words for m <= 4)."""
+    r, P, L = m - 1, 2, 4
+    n = 1 << m
+    fr = I.make_frames(m, r, 300, 1.0, seed=80 + m)
+    out = O.decode(m, r, P, L, I.perm_table(m, r, P, L, seed=4), fr["llr"], want_margin=False)
+    hd = (fr["llr"] < 0).astype(np.uint8)
+    a = np.abs(fr["llr"])
+    odd = np.sum(hd, axis=1) % 2 == 1
+    want = hd.copy()
+    want[np.arange(300)[odd], np.argmin(a, axis=1)[odd]] ^= 1
+    assert np.array_equal(out["cw"], want)
+    np.testing.assert_allclose(out["pm"], np.where(odd, a.min(axis=1), 0.0), rtol=0, atol=1e-12)
+    if n <= 16:
+        words = ((np.arange(1 << n)[:, None] >> np.arange(n)) & 1).astype(np.uint8)
+        book = words[np.sum(words, axis=1) % 2 == 0]
+        idx, _ = _ml_by_enumeration(fr["llr"], book)
+        assert np.array_equal(out["cw"], book[idx])
+
+
 # ------------------------------------------- Aut-SSC node rules (repetition, Wagner SPC) ---
 
 def _ml_by_enumeration(llr, book):

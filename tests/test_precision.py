@@ -3,8 +3,14 @@
 The same seeded frames at the operating points are decoded by the GPU from FP32, FP16 and
 INT8 (step 0.25, saturated at +-127) LLRs and by the FP64 oracle from the exact channel
 LLRs. FP32 decides like FP64 except at near-ties; the quantised inputs change the metric
-itself, so their words may differ wherever the quantisation moves a decision, and the test
-bounds those rates (the measured values are printed and stated in the design notes).
+itself, so their words may differ wherever the quantisation moves a decision.
+
+The bounds follow the measured rates. On these seeded frames every input type decides every
+frame as the FP64 oracle does; the long FER sweeps put the rates against FP32 at about 1e-6
+(FP16) and 5e-5 (INT8, RM(2,9) at 2.25 dB), i.e. an expected 0.003 and 0.15 differing frames
+here. A bound of two frames is therefore far above the expected count (a Poisson count of mean
+0.15 reaches 3 with probability 5e-4) and far below what a broken widening or quantiser
+produces (hundreds of frames).
 """
 import numpy as np
 import pytest
@@ -16,10 +22,10 @@ import oracle as O  # noqa: E402
 import paper_2108_12550_gb300 as pkg  # noqa: E402
 from paper_2108_12550_gb300 import inputs as I  # noqa: E402
 
-# (m, r, P, L, Eb/N0, frames, largest tolerated mismatch rate per input type)
+# (m, r, P, L, Eb/N0, frames, largest tolerated number of frames decided unlike FP64)
 POINTS = [
-    (9, 2, 20, 4, 2.25, 3000, {"f32": 0.01, "f16": 0.03, "i8": 0.10}),
-    (9, 3, 16, 8, 4.0, 600, {"f32": 0.01, "f16": 0.03, "i8": 0.10}),
+    (9, 2, 20, 4, 2.25, 3000, {"f32": 2, "f16": 2, "i8": 2}),
+    (9, 3, 16, 8, 4.0, 600, {"f32": 2, "f16": 2, "i8": 2}),
 ]
 
 
@@ -39,4 +45,4 @@ def test_mismatch_rates_vs_fp64_oracle(m, r, P, L, eb, nf, bound):
         print(f"RM({r},{m}) P={P} L={L} {eb} dB {dt}: decisions differing from FP64 {rates[dt]:.4%} "
               f"(FER {fer:.4%}, FP64 oracle FER {np.mean(np.any(ref['info'] != fr['u'], axis=1)):.4%})")
     for dt, b in bound.items():
-        assert rates[dt] <= b, (dt, rates[dt])
+        assert rates[dt] * nf <= b, (dt, rates[dt] * nf)

@@ -72,6 +72,33 @@ def test_graph_replays_match_direct_decoding():
 
 
 @pytest.mark.gpu
+def test_graph_replay_after_new_permutations_uses_the_new_tables():
+    """rmdec_set_perms followed by a decode overwrites the handle's device tables in place, so
+    a graph captured before still reads valid memory and decodes with the new permutations."""
+    m, r, P, L = 7, 2, 1, 1  # a single decoder at 1 dB: its decisions depend on its table
+    d = pkg.Decoder(m, r, P, L, perm_seed=6)
+    fr = I.make_frames(m, r, 500, 1.0, seed=18)
+    host_in = torch.from_numpy(fr["llr"].astype(np.float32)).pin_memory()
+    host_out = torch.zeros((500, d.kw), dtype=torch.int32).pin_memory()
+    old = d.decode(host_in.cuda()).cpu()
+    g = d.graph(host_in, host_out)
+    g.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(host_out, old)
+    d.set_perms(I.perm_table(m, r, P, L, seed=77))
+    new = d.decode(host_in.cuda()).cpu()  # uploads the new tables
+    other = pkg.Decoder(m, r, P, L, perms=I.perm_table(m, r, P, L, seed=77))
+    assert torch.equal(new, other.decode(host_in.cuda()).cpu())
+    assert not torch.equal(new, old)  # the tables differ in effect on these frames
+    host_out.zero_()
+    g.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(host_out, new)
+    g.close()
+    other.close()
+
+
+@pytest.mark.gpu
 @pytest.mark.parametrize("m,r,P,L", [(9, 2, 20, 4), (7, 2, 8, 4), (9, 3, 16, 8)])
 def test_launch_size_never_changes_results(m, r, P, L):
     """Launches of a few waves run in wider shapes than large ones; every frame must decode
