@@ -370,11 +370,14 @@ PAPER_FER = {"p-FHT-FSCL-4-20": {1.0: 9.80e-3, 1.5: 2.11e-3, 2.0: 2.99e-4, 2.5: 
 # default Eb/N0 points)
 SWEEPS = {
     "rm29": (9, 2, 20, 4, [("p-FHT-FSCL-4-20", "f32", "pfht"), ("p-FHT-FSCL-4-20 FP16 LLRs", "f16", "pfht"),
-                           ("p-FHT-FSCL-4-20 INT8 LLRs", "i8", "pfht"), ("Aut-SSC-512", "f32", "autssc")],
+                           ("p-FHT-FSCL-4-20 INT8 LLRs", "i8", "pfht"),
+                           ("p-FHT-FSCL-4-20 FP16 LLRs tensor-core Hadamard", "f16", "pfht_tc"),
+                           ("Aut-SSC-512", "f32", "autssc")],
              [1.0, 1.5, 2.0, 2.25, 2.5]),
     "rm27": (7, 2, 8, 4, [("p-FHT-FSCL-4-8", "f32", "pfht"), ("p-FHT-FSCL-4-8 INT8 LLRs", "i8", "pfht")],
              [1.0, 1.5, 2.0, 2.5, 3.0, 3.5, 4.0, 4.5, 5.0]),
-    "rm39": (9, 3, 16, 8, [("p-FHT-FSCL-8-16", "f32", "pfht"), ("p-FHT-FSCL-8-16 FP16 LLRs", "f16", "pfht")],
+    "rm39": (9, 3, 16, 8, [("p-FHT-FSCL-8-16", "f32", "pfht"), ("p-FHT-FSCL-8-16 FP16 LLRs", "f16", "pfht"),
+                           ("p-FHT-FSCL-8-16 FP16 LLRs tensor-core Hadamard", "f16", "pfht_tc")],
              [1.0, 1.5, 2.0, 2.5, 3.0]),  # no frame errors in 10^6 frames per point from 3 dB up
 }
 
@@ -401,8 +404,15 @@ def run_fer_sweep(args):
             return lambda x: torch.clamp(torch.round(x / 0.25), -127, 127).to(torch.int8)
         return lambda x: x
 
-    runs = [(name, pkg.Decoder(m, r, 512, algo="autssc", perm_seed=1) if kind == "autssc"
-             else pkg.Decoder(m, r, P, L, perm_seed=1, dtype=dt), convert(dt)) for name, dt, kind in spec]
+    def make(dt, kind):
+        if kind == "autssc":
+            return pkg.Decoder(m, r, 512, algo="autssc", perm_seed=1)
+        d = pkg.Decoder(m, r, P, L, perm_seed=1, dtype=dt)
+        if kind == "pfht_tc":
+            d.set_hadamard("tensor")
+        return d
+
+    runs = [(name, make(dt, kind), convert(dt)) for name, dt, kind in spec]
     fp32_name = spec[0][0]
     gen = torch.Generator(device="cuda")
     chunk = 1 << 18
@@ -492,6 +502,8 @@ def main():
     ap.add_argument("--streams", type=int, default=4, help="serving mix: server CUDA streams")
     ap.add_argument("--frames", type=int, default=0, help="frames per step (default per workload)")
     ap.add_argument("--dtype", default="f32", choices=["f32", "i8", "f16", "i16"])
+    ap.add_argument("--hadamard", default="shuffle", choices=["shuffle", "tensor"],
+                    help="FHT of the FHTL nodes: FP32 butterflies or FP16 tensor-core products")
     ap.add_argument("--cpu-frames", type=int, default=1500, help="CPU-baseline sample size")
     ap.add_argument("--ref-frames", type=int, default=1000, help="frames per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -530,6 +542,8 @@ def main():
     elif args.dtype == "f16":
         llr_np = I.to_f16(llr_np)
     dec = pkg.Decoder(m, r, P, L, perm_seed=1, dtype=args.dtype)
+    if args.hadamard != "shuffle":
+        dec.set_hadamard(args.hadamard)
     x = torch.from_numpy(llr_np).cuda()
     out = torch.empty((nf, dec.kw), dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -610,7 +624,8 @@ def main():
         "config": {"workload": args.workload, "m": m, "r": r, "P": P, "L": L, "n": n, "k": k,
                    "ebn0_db": ebn0, "frames_per_step": nf, "l2": "inputs larger than L2 "
                    f"({llr_np.nbytes / 2**20:.0f} MiB of LLRs per step)", "parallelism": f"replicas{world}",
-                   "launch": dict(zip(("warps_per_cta", "ctas_per_sm"), dec.get_tuning()))},
+                   "launch": dict(zip(("warps_per_cta", "ctas_per_sm"), dec.get_tuning())),
+                   "hadamard": args.hadamard},
         "info_gbit_s": value * k / 1e9,
         "fer_of_timed_batch": fer,
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,

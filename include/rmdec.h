@@ -94,6 +94,22 @@ void rmdec_destroy(rmdec_t h);
  * effect on the next decode; an unknown type returns RMDEC_EINVAL. */
 rmdec_status rmdec_set_dtype(rmdec_t h, rmdec_dtype t);
 
+/* How FHTL nodes (Algorithms 3-4) compute the Walsh-Hadamard spectrum c = H y of their LLRs
+ * (the fast Hadamard transform of Algorithm 4).
+ * SHUFFLE (default): FP32 butterflies in registers and across lanes (warp shuffles).
+ * TENSOR: nodes of 16 to 256 points multiply by H_16 on the tensor cores, with
+ *   H_{2^s} = H_{2^(s-4)} (x) H_16 applied as H_16 X H_16 to the LLRs laid out as a
+ *   2^(s-4) x 16 matrix X (two m16n8k16 MMAs per product): LLRs and the intermediate product
+ *   enter as FP16 (rounded), sums accumulate in FP32, path metrics stay FP32. Smaller nodes
+ *   keep the butterflies. An approximation of the FP32 transform (decisions may differ
+ *   where FP16 rounding moves a candidate); integer inputs are no longer exact. Available
+ *   for RM(2, 9) and RM(3, 9) with L in {4, 8} (RMDEC_EINVAL otherwise). Not groupable. */
+typedef enum {
+    RMDEC_HADAMARD_SHUFFLE = 0,
+    RMDEC_HADAMARD_TENSOR = 1,
+} rmdec_hadamard;
+rmdec_status rmdec_set_hadamard(rmdec_t h, rmdec_hadamard mode);
+
 /* Number of uint16 permutation records the handle holds (11 uint16 per record:
  * [c_0 .. c_9, b] with c_t = A e_t; the record maps index i to b XOR sum_{t: i_t = 1} c_t).
  * p-FHT-FSCL layout: decoder-major, per decoder L initial records then (r-1) * 2L candidate

@@ -51,6 +51,7 @@ def load_library():
         "rmdec_create_fhtfscl": ([ctypes.POINTER(V), I, I, I], I),
         "rmdec_destroy": ([V], None),
         "rmdec_set_dtype": ([V, I], I),
+        "rmdec_set_hadamard": ([V, I], I),
         "rmdec_perm_count": ([V, ctypes.POINTER(I64)], I),
         "rmdec_get_perms": ([V, V, I64], I),
         "rmdec_set_perms": ([V, V, I64], I),
@@ -146,6 +147,11 @@ class Decoder:
     def set_dtype(self, dtype):
         self._check(self._lib.rmdec_set_dtype(self._h, DTYPES[dtype]))
         self.dtype = dtype
+
+    def set_hadamard(self, mode):
+        """'shuffle' (FP32 butterflies, default) or 'tensor' (FP16 tensor-core products)."""
+        self._check(self._lib.rmdec_set_hadamard(self._h, {"shuffle": 0, "tensor": 1}[mode]))
+        self.hadamard = mode
 
     def perm_count(self):
         n = ctypes.c_int64()

@@ -172,9 +172,89 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// ------------------------------------------------------ tensor-core Hadamard ---
+// D = A B + C on the tensor cores, one warp: A 16x16 and B 16x8 in FP16, C and D in FP32
+// (mma.sync m16n8k16). Fragments, with g = lane / 4 and t = lane % 4: A registers hold the
+// element pairs (g, 2t..2t+1), (g+8, 2t..2t+1), (g, 2t+8..2t+9), (g+8, 2t+8..2t+9); B registers
+// (2t..2t+1, g), (2t+8..2t+9, g); C/D (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1).
+__device__ __forceinline__ void mma_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ uint32_t pack_half2(float lo, float hi) {
+    const __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+// entry (i, j) of the Sylvester Hadamard matrix H_16: (-1)^popcount(i & j)
+__device__ __forceinline__ float h16(int i, int j) { return (__popc(i & j) & 1) ? -1.f : 1.f; }
+
+// The Walsh-Hadamard spectrum of a vector x of 2^S <= 256 values (S >= 4), in place, on the
+// tensor cores: with x read as the R x 16 matrix X[a][b] = x[16 a + b] (R = 2^(S-4)), and
+// H_{2^S} = H_R (x) H_16, the spectrum is c[16 p + q] = (H_R X H_16)[p][q]. Both products run as
+// m16n8k16 MMAs with H_16 (exact in FP16) on one side: S = H_16 X (X padded to 16 rows with
+// zeros; rows p < R of H_16 X are H_R X), then C = S H_16, the FP32 accumulators of S
+// rounded to FP16 as the A operand. Inputs enter as FP16 (rounded), sums accumulate in FP32.
+template <int S>
+__device__ __forceinline__ void tc_hadamard(float* x, int lane) {
+    static_assert(S >= 4 && S <= 8, "16 to 256 points");
+    constexpr int R = 1 << (S - 4);
+    const int g = lane >> 2, t = lane & 3;
+    uint32_t ha[4];  // H_16 as the A operand
+    ha[0] = pack_half2(h16(g, 2 * t), h16(g, 2 * t + 1));
+    ha[1] = pack_half2(h16(g + 8, 2 * t), h16(g + 8, 2 * t + 1));
+    ha[2] = pack_half2(h16(g, 2 * t + 8), h16(g, 2 * t + 9));
+    ha[3] = pack_half2(h16(g + 8, 2 * t + 8), h16(g + 8, 2 * t + 9));
+    auto X = [&](int a, int b) { return a < R ? x[16 * a + b] : 0.f; };
+    float sacc[2][4];
+#pragma unroll
+    for (int h = 0; h < 2; h++) {  // S[:, 8h .. 8h + 7] = H_16 X[:, 8h .. 8h + 7]
+        const int col = 8 * h + g;
+        const uint32_t b0 = pack_half2(X(2 * t, col), X(2 * t + 1, col));
+        const uint32_t b1 = pack_half2(X(2 * t + 8, col), X(2 * t + 9, col));
+#pragma unroll
+        for (int i = 0; i < 4; i++) sacc[h][i] = 0.f;
+        mma_16816(sacc[h], ha, b0, b1);
+    }
+    // the accumulators of the two column halves of S are its A fragment
+    uint32_t sa[4];
+    sa[0] = pack_half2(sacc[0][0], sacc[0][1]);
+    sa[1] = pack_half2(sacc[0][2], sacc[0][3]);
+    sa[2] = pack_half2(sacc[1][0], sacc[1][1]);
+    sa[3] = pack_half2(sacc[1][2], sacc[1][3]);
+    float cacc[2][4];
+#pragma unroll
+    for (int h = 0; h < 2; h++) {  // C[:, 8h .. 8h + 7] = S H_16[:, 8h .. 8h + 7]
+        const int col = 8 * h + g;
+        const uint32_t b0 = pack_half2(h16(2 * t, col), h16(2 * t + 1, col));
+        const uint32_t b1 = pack_half2(h16(2 * t + 8, col), h16(2 * t + 9, col));
+#pragma unroll
+        for (int i = 0; i < 4; i++) cacc[h][i] = 0.f;
+        mma_16816(cacc[h], sa, b0, b1);
+    }
+    __syncwarp();  // every lane has read x
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int q = 8 * h + 2 * t;
+        if (g < R) {
+            x[16 * g + q] = cacc[h][0];
+            x[16 * g + q + 1] = cacc[h][1];
+        }
+        if (g + 8 < R) {
+            x[16 * (g + 8) + q] = cacc[h][2];
+            x[16 * (g + 8) + q + 1] = cacc[h][3];
+        }
+    }
+    __syncwarp();
+}
+
 // LOCK: every warp of the block runs one decoder per round, so each leaf can start with a
 // block barrier that keeps the warps on the same code (see fht_leaf).
-template <int M, int R, int L, bool LOCK>
+// TC: FHTL nodes of 16 to 256 points take their spectra from the tensor cores (tc_hadamard)
+// instead of the FP32 butterflies.
+template <int M, int R, int L, bool LOCK, bool TC = false>
 struct Decoder {
     using C = Cfg<M, R, L>;
     static constexpr int N = C::N;
@@ -263,25 +343,36 @@ struct Decoder {
         }
 #pragma unroll
         for (int d = 1; d < G; d <<= 1) A += __shfl_xor_sync(kFull, A, d);
-        // butterflies (u, w) -> (u + w, u - w) over the register bits of the index ...
+        if constexpr (TC && S >= 4 && S <= 8) {
+            // spectra of the L paths from the tensor cores, written over the node's LLRs, then
+            // read back in this leaf's lane layout
+            float* mbuf = w.alpha + C::lvl_off(S);
+            __syncwarp();
+#pragma unroll 1
+            for (int p = 0; p < L; p++) tc_hadamard<S>(mbuf + p * ST, w.lane);
 #pragma unroll
-        for (int h = 1; h < E; h <<= 1)
+            for (int e = 0; e < E; e++) v[e] = act ? buf[l * ST + g + G * e] : 0.f;
+        } else {
+            // butterflies (u, w) -> (u + w, u - w) over the register bits of the index ...
 #pragma unroll
-            for (int e = 0; e < E; e++)
-                if (!(e & h)) {
-                    const float a = v[e], b = v[e + h];
-                    v[e] = a + b;
-                    v[e + h] = a - b;
+            for (int h = 1; h < E; h <<= 1)
+#pragma unroll
+                for (int e = 0; e < E; e++)
+                    if (!(e & h)) {
+                        const float a = v[e], b = v[e + h];
+                        v[e] = a + b;
+                        v[e + h] = a - b;
+                    }
+            // ... and over the lane bits
+#pragma unroll
+            for (int d = 1; d < G; d <<= 1) {
+                // lower index: u + w, upper index: u - w, as o + (+-1) v rounded once
+                const float sg = (g & d) ? -1.f : 1.f;
+#pragma unroll
+                for (int e = 0; e < E; e++) {
+                    const float o = __shfl_xor_sync(kFull, v[e], d);
+                    v[e] = fmaf(sg, v[e], o);
                 }
-        // ... and over the lane bits
-#pragma unroll
-        for (int d = 1; d < G; d <<= 1) {
-            // lower index: u + w, upper index: u - w, as o + (+-1) v rounded once
-            const float sg = (g & d) ? -1.f : 1.f;
-#pragma unroll
-            for (int e = 0; e < E; e++) {
-                const float o = __shfl_xor_sync(kFull, v[e], d);
-                v[e] = fmaf(sg, v[e], o);
             }
         }
         const float pml = __shfl_sync(kFull, ps.pm, l);
@@ -969,10 +1060,10 @@ struct FrameJob {
 // Decodes frame f of a job with the whole block (Algorithm 5 over the P decoders, split
 // round-robin over the warps). The block's records (unless LEAN) and information positions
 // must already be in shared memory; the first barrier also publishes them. LOCK: see Decoder.
-template <int M, int R, int L, bool LOCK>
+template <int M, int R, int L, bool LOCK, bool TC = false>
 __device__ __forceinline__ void decode_frame(const FrameJob& j, const FrameSmem& sm, int64_t f) {
     using C = Cfg<M, R, L>;
-    using D = Decoder<M, R, L, LOCK>;
+    using D = Decoder<M, R, L, LOCK, TC>;
     constexpr int N = C::N;
     constexpr int NW = C::NW;
     const int W = blockDim.x >> 5;
@@ -1091,7 +1182,7 @@ __device__ __forceinline__ void decode_frame(const FrameJob& j, const FrameSmem&
     }
 }
 
-template <int M, int R, int L>
+template <int M, int R, int L, bool TC = false>
 __global__ void __launch_bounds__(32 * kMaxWarps, 1) pfht_kernel(LaunchArgs args) {
     using C = Cfg<M, R, L>;
     extern __shared__ __align__(16) uint8_t smem[];
@@ -1111,7 +1202,7 @@ __global__ void __launch_bounds__(32 * kMaxWarps, 1) pfht_kernel(LaunchArgs args
     j.cw_out = args.cw_out;
     j.pm_out = args.pm_out;
     j.best_out = args.best_out;
-    for (int64_t f = blockIdx.x; f < args.n_frames; f += gridDim.x) decode_frame<M, R, L, true>(j, sm, f);
+    for (int64_t f = blockIdx.x; f < args.n_frames; f += gridDim.x) decode_frame<M, R, L, true, TC>(j, sm, f);
 }
 
 }  // namespace rmdec_dev

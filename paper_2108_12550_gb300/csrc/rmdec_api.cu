@@ -151,6 +151,7 @@ struct rmdec_ctx {
     bool single_start = false;  // FHT-FSCL: identity permutations, one live initial path
     int m = 0, r = 0, P = 0, L = 1, n = 0, k = 0;
     rmdec_dtype dtype = RMDEC_LLR_F32;
+    rmdec_hadamard hadamard = RMDEC_HADAMARD_SHUFFLE;
     std::vector<uint16_t> perms;  // host table in the documented layout
     std::vector<int> info;
     bool dirty = true;
@@ -211,6 +212,7 @@ bool lookup_kernel(rmdec_ctx* h, rmdec_host::KernelEntry* e) {
     using namespace rmdec_host;
     if (h->algo == 1) return lookup_autssc(h->m, h->r, e);
     if (h->algo == 2) return lookup_mlroot(h->m, h->r, e);
+    if (h->hadamard == RMDEC_HADAMARD_TENSOR) return lookup_pfht_tc(h->m, h->r, h->L, e);
     switch (h->m) {
         case 4: return lookup_pfht_m4(h->r, h->L, e);
         case 5: return lookup_pfht_m5(h->r, h->L, e);
@@ -486,6 +488,7 @@ rmdec_status member_info(rmdec_ctx* h, bool prepare, MemberInfo* out) {
     out->k = h->k;
     out->single = h->single_start ? 1 : 0;
     out->dtype = (int)h->dtype;
+    out->hadamard = (int)h->hadamard;
     out->d_recs = h->dirty ? nullptr : h->d_recs;
     out->d_info = h->dirty ? nullptr : h->d_info;
     out->warp_bytes = h->dirty ? 0 : h->kern.warp_bytes;
@@ -543,6 +546,21 @@ rmdec_status rmdec_set_dtype(rmdec_t h, rmdec_dtype t) {
     if (t != RMDEC_LLR_F32 && t != RMDEC_LLR_I8 && t != RMDEC_LLR_F16 && t != RMDEC_LLR_I16)
         return h->fail(RMDEC_EINVAL, "unknown dtype %d", (int)t);
     h->dtype = t;
+    return RMDEC_OK;
+}
+
+rmdec_status rmdec_set_hadamard(rmdec_t h, rmdec_hadamard mode) {
+    if (!h) return RMDEC_EINVAL;
+    if (mode != RMDEC_HADAMARD_SHUFFLE && mode != RMDEC_HADAMARD_TENSOR)
+        return h->fail(RMDEC_EINVAL, "unknown Hadamard mode %d", (int)mode);
+    rmdec_host::KernelEntry e;
+    if (mode == RMDEC_HADAMARD_TENSOR && (h->algo != 0 || !rmdec_host::lookup_pfht_tc(h->m, h->r, h->L, &e)))
+        return h->fail(RMDEC_EINVAL, "no tensor-core Hadamard kernel for this decoder (RM(2|3, 9), L in {4, 8})");
+    if (mode != h->hadamard) {
+        h->hadamard = mode;
+        h->dirty = true;  // the next decode looks up the kernel again
+        h->shape_dirty = true;
+    }
     return RMDEC_OK;
 }
 

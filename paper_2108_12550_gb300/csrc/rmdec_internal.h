@@ -36,6 +36,9 @@ bool lookup_pfht_m8(int r, int L, KernelEntry* e);
 bool lookup_pfht_m9(int r, int L, KernelEntry* e);
 bool lookup_pfht_m10(int r, int L, KernelEntry* e);
 
+// p-FHT-FSCL kernels whose FHTL nodes use the tensor cores (inst_tc.cu).
+bool lookup_pfht_tc(int m, int r, int L, KernelEntry* e);
+
 // Aut-SSC baseline kernels (autssc.cu).
 bool lookup_autssc(int m, int r, KernelEntry* e);
 
@@ -48,6 +51,7 @@ struct MemberInfo {
     int m = 0, r = 0, L = 0, P = 0, n = 0, k = 0;
     int single = 0;
     int dtype = 0;
+    int hadamard = 0;  // rmdec_hadamard of the handle
     const uint16_t* d_recs = nullptr;  // valid after prepare
     const uint16_t* d_info = nullptr;
     int warp_bytes = 0;

@@ -114,3 +114,19 @@ def test_group_membership_is_validated_on_the_host():
     assert lib.rmdec_group_set_tuning(ok._h, -1, 0) == pkg.EINVAL
     assert lib.rmdec_group_set_tuning(ok._h, 20, 0) == pkg.OK
     ok.close()
+
+
+def test_tensor_core_hadamard_availability_is_checked_on_the_host():
+    d = pkg.Decoder(9, 3, 16, 8)
+    d.set_hadamard("tensor")
+    d.set_hadamard("shuffle")
+    for bad in [pkg.Decoder(7, 2, 8, 4), pkg.Decoder(9, 2, 4, 2), pkg.Decoder(9, 2, 8, algo="autssc")]:
+        with pytest.raises(pkg.RmdecError) as ei:
+            bad.set_hadamard("tensor")
+        assert ei.value.status == pkg.EINVAL
+    assert d._lib.rmdec_set_hadamard(d._h, 5) == pkg.EINVAL
+    a = pkg.Decoder(9, 2, 4, 4)
+    a.set_hadamard("tensor")
+    with pytest.raises(pkg.RmdecError):
+        pkg.Group([a])  # grouped launches have no tensor-core variant
+

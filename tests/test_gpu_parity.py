@@ -301,3 +301,45 @@ def test_first_order_and_parity_check_roots_match_the_oracle(m, r, P, L):
     assert np.all(ref["margin"][diff] < 1e-5)  # only FP32 near-ties may decide otherwise
     np.testing.assert_allclose(pm[~diff], ref["pm"][~diff], rtol=1e-5, atol=1e-5 * np.mean(np.abs(fr["llr"])))
 
+
+@pytest.mark.parametrize("m,r,P,L", [(9, 2, 20, 4), (9, 3, 16, 8), (9, 3, 4, 4), (9, 2, 3, 8)])
+def test_tensor_core_hadamard_is_exact_on_small_integer_llrs(m, r, P, L):
+    """The tensor-core transform rounds its operands to FP16, which holds every integer up to
+    2048 exactly. With INT8 codes within +-64 every FHT operand (|alpha| <= 2^(9-s) 64 at a
+    node of 2^s points) and the intermediate H_16 X (<= 32 x 64) stay below that, so the
+    variant must then equal the integer oracle bit for bit: this checks the MMA fragment
+    layouts and the Kronecker factorisation."""
+    fr = I.make_frames(m, r, 400, 2.0, seed=120 + r * 10 + L)
+    perms = I.perm_table(m, r, P, L, seed=9)
+    q = np.clip(I.quantize_i8(fr["llr"] * 0.6), -64, 64).astype(np.int8)
+    ref = O.decode(m, r, P, L, perms, q.astype(np.int64), integer=True, want_margin=False)
+    dec = pkg.Decoder(m, r, P, L, dtype="i8", perms=perms)
+    dec.set_hadamard("tensor")
+    info, cw, pm, best = _gpu_decode(dec, q)
+    assert np.array_equal(cw, ref["cw"]) and np.array_equal(pm.astype(np.int64), ref["pm"])
+    assert np.array_equal(best, ref["best"]) and np.array_equal(info, ref["info"])
+
+
+def test_tensor_core_hadamard_on_fp16_llrs_decides_like_fp32():
+    """RM(3,9), P = 16, L = 8 on FP16 LLRs. With the tensor-core
+    transform the decisions may differ from the FP32 butterflies only where FP16 rounding moves
+    a candidate; on these frames they differ on at most 1% and the path metric stays within
+    1e-2 relative of the returned word's discrepancy."""
+    m, r, P, L = 9, 3, 16, 8
+    fr = I.make_frames(m, r, 600, 2.5, seed=131)
+    perms = I.perm_table(m, r, P, L, seed=2)
+    x = I.to_f16(fr["llr"])
+    dec = pkg.Decoder(m, r, P, L, dtype="f16", perms=perms)
+    ref_info, ref_cw, _, _ = _gpu_decode(dec, x)
+    dec.set_hadamard("tensor")
+    info, cw, pm, best = _gpu_decode(dec, x)
+    diff = np.mean(np.any(cw != ref_cw, axis=1))
+    assert diff <= 0.01, diff
+    y = x.astype(np.float64)
+    np.testing.assert_allclose(pm, _disc(y, cw), rtol=1e-2, atol=1e-2 * np.mean(np.abs(y)))
+    nl = I.noiseless_frames(m, r, 20, seed=3)
+    ni, _, _, _ = _gpu_decode(dec, I.to_f16(nl["llr"]))
+    assert np.array_equal(ni, nl["u"])
+    dec.set_hadamard("shuffle")  # and back
+    assert np.array_equal(_gpu_decode(dec, x)[1], ref_cw)
+

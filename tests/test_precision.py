@@ -2,7 +2,8 @@
 
 The same seeded frames at the operating points are decoded by the GPU from FP32, FP16 and
 INT8 (step 0.25, saturated at +-127) LLRs and by the FP64 oracle from the exact channel
-LLRs. FP32 decides like FP64 except at near-ties; the quantised inputs change the metric
+LLRs, and by the tensor-core Hadamard variant from FP16 LLRs. FP32 decides like FP64 except at
+near-ties; the quantised inputs change the metric
 itself, so their words may differ wherever the quantisation moves a decision.
 
 The bounds follow the measured rates. On these seeded frames every input type decides every
@@ -24,8 +25,8 @@ from paper_2108_12550_gb300 import inputs as I  # noqa: E402
 
 # (m, r, P, L, Eb/N0, frames, largest tolerated number of frames decided unlike FP64)
 POINTS = [
-    (9, 2, 20, 4, 2.25, 3000, {"f32": 2, "f16": 2, "i8": 2}),
-    (9, 3, 16, 8, 4.0, 600, {"f32": 2, "f16": 2, "i8": 2}),
+    (9, 2, 20, 4, 2.25, 3000, {"f32": 2, "f16": 2, "i8": 2, "f16_tensor_hadamard": 2}),
+    (9, 3, 16, 8, 4.0, 600, {"f32": 2, "f16": 2, "i8": 2, "f16_tensor_hadamard": 2}),
 ]
 
 
@@ -34,10 +35,13 @@ def test_mismatch_rates_vs_fp64_oracle(m, r, P, L, eb, nf, bound):
     fr = I.make_frames(m, r, nf, eb, seed=4242)
     perms = I.perm_table(m, r, P, L, seed=1)
     ref = O.decode(m, r, P, L, perms, fr["llr"])
-    inputs = {"f32": fr["llr"].astype(np.float32), "f16": I.to_f16(fr["llr"]), "i8": I.quantize_i8(fr["llr"])}
+    inputs = {"f32": fr["llr"].astype(np.float32), "f16": I.to_f16(fr["llr"]), "i8": I.quantize_i8(fr["llr"]),
+              "f16_tensor_hadamard": I.to_f16(fr["llr"])}
     rates = {}
     for dt, x in inputs.items():
-        dec = pkg.Decoder(m, r, P, L, dtype=dt, perms=perms)
+        dec = pkg.Decoder(m, r, P, L, dtype=dt[:3], perms=perms)
+        if dt.endswith("tensor_hadamard"):
+            dec.set_hadamard("tensor")
         out = dec.decode(torch.from_numpy(x).cuda()).cpu().numpy()
         info = pkg.unpack_bits(out, dec.k)
         rates[dt] = float(np.mean(np.any(info != ref["info"], axis=1)))
