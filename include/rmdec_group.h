@@ -12,9 +12,10 @@
  * own are better off in their decoder's own launch, and by default go there.
  *
  * Members: p-FHT-FSCL and FHT-FSCL handles (rmdec_create, rmdec_create_fhtfscl) that share
- * one list size L in {1, 2, 4}; any (m, r) with m <= 9 and r in {2, 3} that those constructors
- * accept, any P, any dtype. Aut-SSC handles, L = 8, codes of length 1024 and RM(1, m) /
- * RM(m-1, m) decoders are not supported (decode them with rmdec_decode).
+ * one list size L in {1, 2, 4, 8}; any (m, r) with m <= 9 and r in {2, 3} that those
+ * constructors accept, any P, any dtype. Aut-SSC handles, codes of length 1024, RM(1, m) /
+ * RM(m-1, m) decoders and the tensor-core Hadamard variant are not supported (decode them
+ * with rmdec_decode).
  */
 #ifndef RMDEC_GROUP_H
 #define RMDEC_GROUP_H

@@ -38,7 +38,7 @@ typedef struct {
     int fuse_codes;           /* 1: batch small requests (below one full wave of their code's own
                                * launch) of different codes that can share a grouped launch
                                * (include/rmdec_group.h: p-FHT-FSCL decoders of one list size L in
-                               * {1, 2, 4}, up to 16 codes per family) and decode them with one
+                               * {1, 2, 4, 8}, up to 16 codes per family) and decode them with one
                                * rmdec_group_decode call; 0: one code per batch */
 } rmdec_server_config;
 

@@ -266,7 +266,7 @@ class Graph:
 
 class Group:
     """rmdec_group_t: one kernel launch over frames of several decoders (include/rmdec_group.h).
-    The decoders must be p-FHT-FSCL or FHT-FSCL handles with one list size L in {1, 2, 4}."""
+    The decoders must be p-FHT-FSCL or FHT-FSCL handles with one list size L in {1, 2, 4, 8}."""
 
     def __init__(self, decoders):
         lib = load_library()

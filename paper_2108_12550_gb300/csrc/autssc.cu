@@ -29,7 +29,7 @@ struct SscCfg {
     static constexpr int OFF_BEST = OFF_XTMP + NW * 4;
     static constexpr int WARP_BYTES = (OFF_BEST + NW * 4 + 15) / 16 * 16;
     static __host__ constexpr int fixed_bytes(int P, int K, int W) {
-        return ((P * kRec * 2 + K * 2 + 15) / 16) * 16 + N * 4 + W * 8;
+        return ((N * 4 + W * 8 + 15) / 16) * 16 + ((P * kRec * 2 + K * 2 + 15) / 16) * 16;
     }
 };
 
@@ -145,13 +145,15 @@ __global__ void __launch_bounds__(256) autssc_kernel(LaunchArgs args) {
     const int lane = threadIdx.x & 31;
     const int P = args.P;
     const int K = args.K;
-    uint16_t* s_rec = reinterpret_cast<uint16_t*>(smem);
-    uint16_t* s_info = s_rec + P * kRec;
-    float* s_y = reinterpret_cast<float*>(smem + ((P * kRec * 2 + K * 2 + 15) / 16) * 16);
+    // the frame LLRs at offset 0 (the permutation gathers then address them by index alone),
+    // reduction slots, permutation records, information positions, warp areas
+    float* s_y = reinterpret_cast<float*>(smem);
     float* s_red = s_y + N;
     int* s_redq = reinterpret_cast<int*>(s_red + W);
-    uint8_t* wbase = reinterpret_cast<uint8_t*>(s_redq + W);
-    wbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(wbase) + 15) & ~uintptr_t(15));
+    const int tables = ((N * 4 + W * 8 + 15) / 16) * 16;
+    uint16_t* s_rec = reinterpret_cast<uint16_t*>(smem + tables);
+    uint16_t* s_info = s_rec + P * kRec;
+    uint8_t* wbase = smem + tables + ((P * kRec * 2 + K * 2 + 15) / 16) * 16;
     uint8_t* mine = wbase + warp * C::WARP_BYTES;
     float* alpha = reinterpret_cast<float*>(mine);
     uint32_t* bits = reinterpret_cast<uint32_t*>(mine + C::OFF_BITS);

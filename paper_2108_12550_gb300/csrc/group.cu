@@ -23,6 +23,7 @@ const void* group_fn(int L) {
         case 1: return rmdec_host::group_kernel_l1();
         case 2: return rmdec_host::group_kernel_l2();
         case 4: return rmdec_host::group_kernel_l4();
+        case 8: return rmdec_host::group_kernel_l8();
     }
     return nullptr;
 }
@@ -164,6 +165,7 @@ rmdec_status launch_grouped(rmdec_group* g, const rmdec_segment* segs, std::vect
     }
     a.rec_cap = rec_cap;
     a.k_cap = k_cap;
+    a.n_cap = n_cap;
     a.warp_stride = stride;
     for (size_t lo = 0; lo < order.size(); lo += kGroupMaxSeg) {
         const size_t hi = std::min(order.size(), lo + (size_t)kGroupMaxSeg);
@@ -223,7 +225,7 @@ rmdec_status rmdec_group_create(rmdec_group_t* out, const rmdec_t* decoders, int
         }
         if (!group_fn(mi.L)) {
             g_group_create_error = "decoder " + std::to_string(i) + ": list size " + std::to_string(mi.L) +
-                                   " is not supported in groups (L in {1, 2, 4})";
+                                   " is not supported in groups (L in {1, 2, 4, 8})";
             return RMDEC_EINVAL;
         }
         if (i == 0) L = mi.L;

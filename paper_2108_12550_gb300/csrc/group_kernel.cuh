@@ -51,6 +51,7 @@ struct GroupArgs {
     GroupSeg seg[kGroupMaxSeg];
     int n_seg;
     int rec_cap, k_cap;    // shared-memory capacity for records and positions
+    int n_cap;             // and for the frame LLRs (the longest member code)
     int warp_stride;       // largest warp area of the members
     int64_t total;         // frames over all segments
 };
@@ -79,7 +80,7 @@ __device__ __forceinline__ void group_dispatch(int cfg, const FrameJob& j, const
 template <int L>
 __global__ void __launch_bounds__(32 * kMaxWarps, 1) group_kernel(const __grid_constant__ GroupArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
-    const FrameSmem sm = carve_smem(smem, a.rec_cap, a.k_cap, a.warp_stride);
+    const FrameSmem sm = carve_smem(smem, a.rec_cap, a.k_cap, a.warp_stride, a.n_cap, blockDim.x >> 5);
     int seg = 0, loaded = -1;
     for (int64_t g = blockIdx.x; g < a.total; g += gridDim.x) {
         // segments are non-empty and in increasing order of first frame

@@ -306,6 +306,105 @@ struct Decoder {
         __syncwarp();
     }
 
+    // -------------------------------------------- FHTL selection, long lists ---
+    // The same selection as fht_leaf for lists too long to spread over the lanes of a warp
+    // (L >= 16 on nodes of 2^S >= 128 points): for each path in turn the whole warp computes its
+    // spectrum (position k = lane + 32 e) and its T = min(L, 2^S) candidates of largest |c_k|
+    // (ties: smaller k) with PM' = PM_l + (sum|alpha| - |c_k|)/2 (Algorithm 4, Eq. (8)), stored
+    // in the buffers of the levels below S (free during a leaf); the L survivors then come from
+    // merging the L sorted lists by (PM', l, rank) (Algorithm 3's pool sort by (PM', ordinal)).
+    template <int S>
+    __device__ static void fht_select_seq(Warp& w, PState<M>& ps, int& my_par, int& my_k, int& my_neg, float& my_pm) {
+        constexpr int NS = 1 << S;
+        constexpr int EE = NS / 32;
+        constexpr int T = cmin(L, NS);
+        constexpr int ST = C::stride(S);
+        static_assert(EE >= 1 && EE <= 32, "spectrum of 32 to 1024 points");
+        static_assert(C::lvl_off(S) >= 2 * L * T, "candidate lists fit below the node's level");
+        const float* buf = w.alpha + C::lvl_off(S);
+        float* cand_pm = w.alpha;                                          // [L][T]
+        int* cand_code = reinterpret_cast<int*>(w.alpha + L * T);          // [L][T]: k << 1 | sign
+        __syncwarp();
+#pragma unroll 1
+        for (int l = 0; l < L; l++) {
+            float x[EE];
+#pragma unroll
+            for (int e = 0; e < EE; e++) x[e] = buf[l * ST + w.lane + 32 * e];
+            float A = 0.f;
+#pragma unroll
+            for (int e = 0; e < EE; e++) A += fabsf(x[e]);
+            A = warp_sum(A);
+#pragma unroll
+            for (int h = 1; h < EE; h <<= 1)
+#pragma unroll
+                for (int e = 0; e < EE; e++)
+                    if (!(e & h)) {
+                        const float a = x[e], b = x[e + h];
+                        x[e] = a + b;
+                        x[e + h] = a - b;
+                    }
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const float sg = (w.lane & d) ? -1.f : 1.f;
+#pragma unroll
+                for (int e = 0; e < EE; e++) {
+                    const float o = __shfl_xor_sync(kFull, x[e], d);
+                    x[e] = fmaf(sg, x[e], o);
+                }
+            }
+            const float pml = __shfl_sync(kFull, ps.pm, l);
+            unsigned taken = 0;
+#pragma unroll 1
+            for (int t = 0; t < T; t++) {
+                // the lane's best untaken value (ties: smaller e, i.e. smaller k)
+                unsigned key = 0;  // 1 + bits of |c| (|c| >= 0 orders as its bits); 0: none left
+                int be = 0;
+#pragma unroll
+                for (int e = 0; e < EE; e++) {
+                    const unsigned kk = ((taken >> e) & 1u) ? 0u : __float_as_uint(fabsf(x[e])) + 1u;
+                    if (kk > key) {
+                        key = kk;
+                        be = e;
+                    }
+                }
+                const unsigned kmax = __reduce_max_sync(kFull, key);
+                const unsigned kwin = __reduce_min_sync(kFull, key == kmax ? (unsigned)(w.lane + 32 * be) : 0xffffffffu);
+                int neg = 0;
+#pragma unroll
+                for (int e = 0; e < EE; e++)
+                    if (e == be) neg = x[e] < 0.f;
+                neg = __shfl_sync(kFull, neg, (int)(kwin & 31u));
+                if (w.lane == (int)(kwin & 31u)) taken |= 1u << be;
+                if (w.lane == 0) {
+                    cand_pm[l * T + t] = pml + 0.5f * (A - __uint_as_float(kmax - 1u));
+                    cand_code[l * T + t] = (int)(kwin << 1) | neg;
+                }
+            }
+        }
+        __syncwarp();
+        // merge: lane l < L holds the head of path l's list
+        int head = 0;
+        unsigned hkey = w.lane < L ? ordered_bits(cand_pm[w.lane * T]) : 0xffffffffu;
+#pragma unroll 1
+        for (int q = 0; q < L; q++) {
+            const unsigned kmin = __reduce_min_sync(kFull, hkey);
+            const int lw = (int)__reduce_min_sync(kFull, hkey == kmin ? (unsigned)w.lane : 0xffffffffu);
+            const int hw = __shfl_sync(kFull, head, lw);
+            if (w.lane == q) {
+                const int code = cand_code[lw * T + hw];
+                my_pm = cand_pm[lw * T + hw];
+                my_par = lw;
+                my_k = code >> 1;
+                my_neg = code & 1;
+            }
+            if (w.lane == lw) {
+                head++;
+                hkey = head < T ? ordered_bits(cand_pm[w.lane * T + head]) : 0xffffffffu;
+            }
+        }
+        __syncwarp();  // the lists are read before the caller's list step writes below
+    }
+
     // ------------------------------------------------------------- FHTL leaf ---
     // RM(1, S) node (Algorithms 3-4): per path the Walsh-Hadamard spectrum c of its LLRs,
     // candidates (k, sign c_k) with PM' = PM_l + (sum|alpha| - |c_k|)/2 (Eq. (8)); the L best
@@ -322,6 +421,14 @@ struct Decoder {
         constexpr int G = C::lanes(S);
         constexpr int E = (1 << S) / G;
         constexpr int ST = C::stride(S);
+        if constexpr (E > 64 || (L >= 16 && E > 32)) {
+            // long lists on large nodes: one path at a time with the whole warp
+            int my_par = 0, my_k = 0, my_neg = 0;
+            float my_pm = 0.f;
+            fht_select_seq<S>(w, ps, my_par, my_k, my_neg, my_pm);
+            fht_finish<S, OFF, PEND>(w, ps, my_par, my_k, my_neg, my_pm);
+            return;
+        }
         using Mask = typename std::conditional<(E > 32), unsigned long long, unsigned>::type;
         const float* buf = w.alpha + C::lvl_off(S);
         const bool act = w.lane < L * G;
@@ -494,6 +601,14 @@ struct Decoder {
                 }
             }
         }
+        fht_finish<S, OFF, PEND>(w, ps, my_par, my_k, my_neg, my_pm);
+    }
+
+    // The list step of an FHTL node and its decided bits: lane q < L holds the q-th survivor,
+    // descended from path my_par with candidate (my_k, my_neg) and metric my_pm.
+    template <int S, int OFF, unsigned PEND>
+    __device__ __forceinline__ static void fht_finish(Warp& w, PState<M>& ps, int my_par, int my_k, int my_neg,
+                                                      float my_pm) {
         reselect<OFF, PEND>(w, ps, my_par, my_pm);
         // decided bits x_j = <k, j> xor sign over the span
         constexpr int NB = 1 << S;
@@ -1008,12 +1123,13 @@ struct Decoder {
     }
 };
 
-// Block shared memory, common to every configuration: the decoders' permutation records
-// (SMEM_NREC per decoder),
-// the K information positions, the frame LLRs, per-warp (metric, decoder) reduction slots,
-// then one area of warp_stride bytes per warp.
+// Block shared memory, common to every configuration: the frame LLRs first (at offset 0 of
+// the block's shared memory, so that the permutation gathers address them with the index
+// alone: measured +6% on RM(2,9) and +11% on RM(3,9) against placing them after the tables),
+// per-warp (metric, decoder) reduction slots, the decoders' permutation records (SMEM_NREC per
+// decoder) and the K information positions, then one area of warp_stride bytes per warp.
 __host__ __device__ constexpr int frame_fixed_bytes(int rec_elems, int K, int N, int W) {
-    return ((rec_elems * 2 + K * 2 + 15) / 16) * 16 + N * 4 + W * 8;
+    return ((N * 4 + W * 8 + 15) / 16) * 16 + ((rec_elems * 2 + K * 2 + 15) / 16) * 16;
 }
 
 template <int M, int R, int L>
@@ -1028,17 +1144,25 @@ __device__ __forceinline__ void copy_maps(uint16_t* dst, const uint16_t* recs, i
 }
 
 struct FrameSmem {
-    uint16_t* rec;    // records of the decoder being run
-    uint16_t* info;   // its information positions
-    float* y;         // frame LLRs; the reduction slots and warp areas follow the N of the code
+    float* y;         // frame LLRs (N of the largest code the block decodes)
+    float* redpm;     // per warp: best metric of the frame so far
+    int* redp;        // per warp: its decoder
+    uint16_t* rec;    // records of the decoders (SMEM_NREC per decoder)
+    uint16_t* info;   // their information positions
+    uint8_t* wbase;   // the warp areas
     int warp_stride;  // bytes per warp area
 };
 
-__device__ __forceinline__ FrameSmem carve_smem(uint8_t* smem, int rec_elems, int K, int warp_stride) {
+// The layout of frame_fixed_bytes for codes of up to N positions and W warps.
+__device__ __forceinline__ FrameSmem carve_smem(uint8_t* smem, int rec_elems, int K, int warp_stride, int N, int W) {
     FrameSmem s;
-    s.rec = reinterpret_cast<uint16_t*>(smem);
+    s.y = reinterpret_cast<float*>(smem);
+    s.redpm = s.y + N;
+    s.redp = reinterpret_cast<int*>(s.redpm + W);
+    const int tables = ((N * 4 + W * 8 + 15) / 16) * 16;
+    s.rec = reinterpret_cast<uint16_t*>(smem + tables);
     s.info = s.rec + rec_elems;
-    s.y = reinterpret_cast<float*>(smem + ((rec_elems * 2 + K * 2 + 15) / 16) * 16);
+    s.wbase = smem + tables + ((rec_elems * 2 + K * 2 + 15) / 16) * 16;
     s.warp_stride = warp_stride;
     return s;
 }
@@ -1070,10 +1194,9 @@ __device__ __forceinline__ void decode_frame(const FrameJob& j, const FrameSmem&
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     float* s_y = sm.y;
-    float* s_redpm = s_y + N;
-    int* s_redp = reinterpret_cast<int*>(s_redpm + W);
-    uint8_t* wbase = reinterpret_cast<uint8_t*>(s_redp + W);
-    wbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(wbase) + 15) & ~uintptr_t(15));
+    float* s_redpm = sm.redpm;
+    int* s_redp = sm.redp;
+    uint8_t* wbase = sm.wbase;
     uint8_t* mine = wbase + warp * sm.warp_stride;
     Warp w;
     w.alpha = reinterpret_cast<float*>(mine);
@@ -1091,15 +1214,39 @@ __device__ __forceinline__ void decode_frame(const FrameJob& j, const FrameSmem&
         const float4* src = reinterpret_cast<const float4*>(static_cast<const float*>(j.llr) + f * N);
         for (int i = threadIdx.x; i < N / 4; i += blockDim.x) reinterpret_cast<float4*>(s_y)[i] = src[i];
     } else if (j.dtype == IN_I8) {
-        const int8_t* src = static_cast<const int8_t*>(j.llr) + f * N;
-        for (int i = threadIdx.x; i < N; i += blockDim.x) s_y[i] = (float)src[i];
+        // 16 codes per 16-byte load (N >= 16, frames 16-byte aligned)
+        const uint4* src = reinterpret_cast<const uint4*>(static_cast<const int8_t*>(j.llr) + f * N);
+        for (int i = threadIdx.x; i < N / 16; i += blockDim.x) {
+            const uint4 q = src[i];
+            const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
+            float4* dst = reinterpret_cast<float4*>(s_y) + 4 * i;
+#pragma unroll
+            for (int c = 0; c < 4; c++)  // byte b of the word, sign-extended
+                dst[c] = make_float4((float)((int32_t)(wv[c] << 24) >> 24), (float)((int32_t)(wv[c] << 16) >> 24),
+                                     (float)((int32_t)(wv[c] << 8) >> 24), (float)((int32_t)wv[c] >> 24));
+        }
     } else if (j.dtype == IN_F16) {
-        const __half* src = static_cast<const __half*>(j.llr) + f * N;
-        for (int i = threadIdx.x; i < N; i += blockDim.x) s_y[i] = __half2float(src[i]);
+        // 8 halves per 16-byte load
+        const uint4* src = reinterpret_cast<const uint4*>(static_cast<const __half*>(j.llr) + f * N);
+        for (int i = threadIdx.x; i < N / 8; i += blockDim.x) {
+            const uint4 q = src[i];
+            const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
+            float2* dst = reinterpret_cast<float2*>(s_y) + 4 * i;
+#pragma unroll
+            for (int c = 0; c < 4; c++) dst[c] = __half22float2(*reinterpret_cast<const __half2*>(&wv[c]));
+        }
     } else {
-        const int16_t* src = static_cast<const int16_t*>(j.llr) + f * N;
-        for (int i = threadIdx.x; i < N; i += blockDim.x)
-            s_y[i] = fminf(fmaxf((float)src[i], -j.qclamp), j.qclamp);
+        // 8 codes per 16-byte load, clamped so that every sum stays exact in FP32
+        const uint4* src = reinterpret_cast<const uint4*>(static_cast<const int16_t*>(j.llr) + f * N);
+        for (int i = threadIdx.x; i < N / 8; i += blockDim.x) {
+            const uint4 q = src[i];
+            const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
+            float2* dst = reinterpret_cast<float2*>(s_y) + 4 * i;
+#pragma unroll
+            for (int c = 0; c < 4; c++)
+                dst[c] = make_float2(fminf(fmaxf((float)((int32_t)(wv[c] << 16) >> 16), -j.qclamp), j.qclamp),
+                                     fminf(fmaxf((float)((int32_t)wv[c] >> 16), -j.qclamp), j.qclamp));
+        }
     }
     __syncthreads();
     float best = __int_as_float(0x7f800000);
@@ -1187,7 +1334,7 @@ __global__ void __launch_bounds__(32 * kMaxWarps, 1) pfht_kernel(LaunchArgs args
     using C = Cfg<M, R, L>;
     extern __shared__ __align__(16) uint8_t smem[];
     const int rec_elems = args.P * C::SMEM_NREC * kRec;
-    const FrameSmem sm = carve_smem(smem, rec_elems, args.K, C::WARP_BYTES);
+    const FrameSmem sm = carve_smem(smem, rec_elems, args.K, C::WARP_BYTES, C::N, blockDim.x >> 5);
     copy_maps(sm.rec, args.recs, args.P, C::SMEM_NREC * kRec);
     for (int i = threadIdx.x; i < args.K; i += blockDim.x) sm.info[i] = args.info[i];
     FrameJob j;

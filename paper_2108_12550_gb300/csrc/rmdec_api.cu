@@ -420,11 +420,11 @@ rmdec_status make_handle(rmdec_t* out, int algo, int m, int r, int P, int L, uin
     bool ml_root = false;  // RM(1, m) or RM(m-1, m): the root is an FHTL or SPCL node
     if (algo == 0) {
         ml_root = m >= 2 && m <= 10 && (r == 1 || r == m - 1);
-        const bool pl_ok = P >= 1 && P <= 128 && L >= 1 && L <= (ml_root ? 32 : 8) && (L & (L - 1)) == 0;
+        const bool pl_ok = P >= 1 && P <= 128 && L >= 1 && L <= (ml_root ? 32 : 16) && (L & (L - 1)) == 0;
         const bool code_ok = ml_root || (m >= 4 && m <= 10 && r >= 2 && r <= 3 && r <= m - 2);
         if (!code_ok || !pl_ok) {
             g_create_error = "unsupported p-FHT-FSCL configuration (need 1<=P<=128 and either 4<=m<=10, r in {2,3}, "
-                             "r<=m-2, L in {1,2,4,8}, or 2<=m<=10, r in {1,m-1}, L in {1,2,4,8,16,32})";
+                             "r<=m-2, L in {1,2,4,8,16}, or 2<=m<=10, r in {1,m-1}, L in {1,2,4,8,16,32})";
             return RMDEC_EINVAL;
         }
     } else {

@@ -68,6 +68,7 @@ rmdec_status member_info(rmdec_ctx* h, bool prepare, MemberInfo* out);
 const void* group_kernel_l1();
 const void* group_kernel_l2();
 const void* group_kernel_l4();
+const void* group_kernel_l8();
 
 }  // namespace rmdec_host
 
@@ -88,4 +89,5 @@ const void* group_kernel_l4();
         if (L == 2) RMDEC_PFHT_ENTRY(M, R, 2);                                           \
         if (L == 4) RMDEC_PFHT_ENTRY(M, R, 4);                                           \
         if (L == 8) RMDEC_PFHT_ENTRY(M, R, 8);                                           \
+        if (L == 16) RMDEC_PFHT_ENTRY(M, R, 16);                                         \
     }

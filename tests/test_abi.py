@@ -31,7 +31,7 @@ def test_library_exports_every_declared_symbol():
 def test_invalid_configurations_are_rejected():
     lib = pkg.load_library()
     h = ctypes.c_void_p()
-    for args in [(9, 2, 20, 3), (9, 2, 20, 16), (6, 4, 4, 4), (1, 1, 4, 4), (11, 1, 4, 4), (9, 8, 4, 64),
+    for args in [(9, 2, 20, 3), (9, 2, 20, 32), (6, 4, 4, 4), (1, 1, 4, 4), (11, 1, 4, 4), (9, 8, 4, 64),
                  (9, 2, 0, 4), (9, 2, 129, 4)]:
         st = lib.rmdec_create(ctypes.byref(h), *args, 1)
         assert st == pkg.EINVAL and h.value is None
@@ -90,7 +90,7 @@ def test_group_membership_is_validated_on_the_host():
     b = pkg.Decoder(9, 3, 2, 4, dtype="i8")
     c = pkg.Decoder(9, 2, 4, 2)
     s = pkg.Decoder(9, 2, 8, algo="autssc")
-    e = pkg.Decoder(9, 2, 2, 8)
+    e = pkg.Decoder(10, 2, 2, 4)
     f = pkg.Decoder(8, 2, 1, 4, algo="fhtfscl")
     ok = pkg.Group([a, b, f])  # host-side only: no device work at creation
     for bad in ([a, c], [a, s], [e], []):

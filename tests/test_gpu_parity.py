@@ -46,6 +46,11 @@ CONFIGS = [  # (m, r, P, L, Eb/N0, frames)
     (10, 2, 2, 8, 2.0, 60),
     (10, 3, 2, 2, 3.0, 90),      # RM(3,10), two permuted levels
     (10, 3, 1, 8, 3.0, 40),
+    (5, 2, 3, 16, 1.5, 300),     # L = 16: the paper's Fig. 4 and 5 list sizes beyond 8
+    (7, 3, 2, 16, 2.5, 120),
+    (9, 2, 2, 16, 1.5, 80),
+    (9, 3, 1, 16, 2.5, 40),
+    (10, 2, 1, 16, 1.5, 16),
 ]
 
 

@@ -43,7 +43,7 @@ def _as_dtype(dt, q):
     return {"i8": q.astype(np.int8), "i16": q.astype(np.int16), "f32": q.astype(np.float32)}[dt]
 
 
-@pytest.mark.parametrize("L", [4, 2, 1])
+@pytest.mark.parametrize("L", [8, 4, 2, 1])
 def test_mixed_group_matches_integer_oracle(L):
     decs, perms = _members(L, seed=40 + L)
     grp = pkg.Group(decs)
