@@ -582,15 +582,17 @@ struct Decoder {
                             h1 = h1 || g1;
                         };
                         if constexpr (M >= 9 && L <= 4) {
-                            // from a local copy with a rolled loop: 16% less code for the
-                            // m = 9 trees, whose code exceeds the instruction caches (measured
-                            // +1%); with L = 8 rescans are frequent enough, and smaller trees
-                            // fit the caches, so the unrolled form below is faster there
-                            float vloc[E];
+                            // a rolled loop over the lane's spectrum parked in its own slots of
+                            // the leaf's shared-memory buffer (read only at the start of the
+                            // leaf): 16% less code for the m = 9 trees, whose code exceeds the
+                            // instruction caches, and no local memory; with L = 8 rescans are
+                            // frequent enough, and smaller trees fit the caches, so the
+                            // unrolled form below is faster there
+                            float* mine = w.alpha + C::lvl_off(S) + l * ST + g;
 #pragma unroll
-                            for (int e = 0; e < E; e++) vloc[e] = v[e];
+                            for (int e = 0; e < E; e++) mine[G * e] = v[e];
 #pragma unroll 1
-                            for (int e = 0; e < E; e++) visit(e, vloc[e]);
+                            for (int e = 0; e < E; e++) visit(e, mine[G * e]);
                         } else {
 #pragma unroll
                             for (int e = 0; e < E; e++) visit(e, v[e]);
