@@ -13,9 +13,9 @@
  *
  * Members: p-FHT-FSCL and FHT-FSCL handles (rmdec_create, rmdec_create_fhtfscl) that share
  * one list size L in {1, 2, 4, 8}; any (m, r) with m <= 9 and r in {2, 3} that those
- * constructors accept, any P, any dtype. Aut-SSC handles, codes of length 1024, RM(1, m) /
- * RM(m-1, m) decoders and the tensor-core Hadamard variant are not supported (decode them
- * with rmdec_decode).
+ * constructors accept, any P, any dtype. Aut-SSC handles, codes of length 1024, RM(4, m),
+ * RM(1, m) / RM(m-1, m) decoders and the tensor-core Hadamard variant are not supported
+ * (decode them with rmdec_decode).
  */
 #ifndef RMDEC_GROUP_H
 #define RMDEC_GROUP_H

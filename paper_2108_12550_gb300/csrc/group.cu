@@ -219,6 +219,10 @@ rmdec_status rmdec_group_create(rmdec_group_t* out, const rmdec_t* decoders, int
             g_group_create_error = "decoder " + std::to_string(i) + ": tensor-core Hadamard decoders are not supported in groups";
             return RMDEC_EINVAL;
         }
+        if (mi.r > 3) {
+            g_group_create_error = "decoder " + std::to_string(i) + ": RM(4, m) decoders are not supported in groups";
+            return RMDEC_EINVAL;
+        }
         if (mi.m > 9) {
             g_group_create_error = "decoder " + std::to_string(i) + ": codes longer than 512 are not supported in groups";
             return RMDEC_EINVAL;

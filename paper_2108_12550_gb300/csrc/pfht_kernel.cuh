@@ -780,9 +780,11 @@ struct Decoder {
         constexpr int C2 = 2 * L;
         constexpr int HALF = 1 << (S - 1);
         float mylm = 0.f;  // lane c keeps LM_c
-        if constexpr (M >= 9) {
+        if constexpr (M >= 9 && !(M == 9 && L == 8)) {
             // candidates two at a time, each with a warp sum (the m = 9 trees exceed the
-            // instruction caches: the fully unrolled form below measured 2% slower there)
+            // instruction caches: the fully unrolled form below measured 2-3.5% slower for
+            // RM(2,9) with L = 4, but 3% faster for RM(3,9) with L = 8; longer lists and
+            // longer codes spill in it)
 #pragma unroll 2
             for (int c = 0; c < C2; c++) {
                 const uint16_t* r = recs + c * kRec;

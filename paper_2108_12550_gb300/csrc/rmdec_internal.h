@@ -35,6 +35,9 @@ bool lookup_pfht_m7(int r, int L, KernelEntry* e);
 bool lookup_pfht_m8(int r, int L, KernelEntry* e);
 bool lookup_pfht_m9(int r, int L, KernelEntry* e);
 bool lookup_pfht_m10(int r, int L, KernelEntry* e);
+// RM(4, m): three permuted levels (inst_r4_*.cu)
+bool lookup_pfht_r4_small(int m, int L, KernelEntry* e);  // m = 6, 7, 8
+bool lookup_pfht_r4_m9(int L, KernelEntry* e);
 
 // p-FHT-FSCL kernels whose FHTL nodes use the tensor cores (inst_tc.cu).
 bool lookup_pfht_tc(int m, int r, int L, KernelEntry* e);

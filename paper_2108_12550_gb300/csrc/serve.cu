@@ -402,7 +402,7 @@ rmdec_status rmdec_server_add_decoder(rmdec_server_t s, rmdec_t h, int* code_id)
     std::lock_guard<std::mutex> g(s->mu);
     const int id = (int)s->codes.size();
     int fam = -1, member = 0;
-    if (s->cfg.fuse_codes && mi.algo == 0 && mi.m <= 9 && mi.hadamard == 0 && (mi.L == 1 || mi.L == 2 || mi.L == 4 || mi.L == 8)) {
+    if (s->cfg.fuse_codes && mi.algo == 0 && mi.m <= 9 && mi.r <= 3 && mi.hadamard == 0 && (mi.L == 1 || mi.L == 2 || mi.L == 4 || mi.L == 8)) {
         for (int f = 0; f < (int)s->families.size(); f++)
             if (s->families[f].L == mi.L && s->families[f].codes.size() < 16) fam = f;
         if (fam < 0) {

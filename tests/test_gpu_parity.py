@@ -51,6 +51,10 @@ CONFIGS = [  # (m, r, P, L, Eb/N0, frames)
     (9, 2, 2, 16, 1.5, 80),
     (9, 3, 1, 16, 2.5, 40),
     (10, 2, 1, 16, 1.5, 16),
+    (6, 4, 3, 2, 2.0, 400),      # RM(4, m): three permuted levels (the paper's Fig. 4 and 5 codes)
+    (7, 4, 2, 16, 3.0, 100),
+    (8, 4, 4, 4, 3.0, 200),
+    (9, 4, 2, 8, 3.5, 60),
 ]
 
 
