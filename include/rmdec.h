@@ -52,8 +52,8 @@ typedef enum {
 /* Creates a p-FHT-FSCL-L-P decoder for RM(r, m) (Algorithm 5 with Algorithm 2 per decoder).
  * Supported, with 1 <= P <= 128:
  *   - 4 <= m <= 10, r in {2, 3} with r <= m - 2, and 6 <= m <= 9, r = 4 (the root is a
- *     permuted node, 1 < r < m - 1; r - 1 permuted levels), L in {1, 2, 4, 8, 16}
- *     (P = M_1 = 100, L = 1 is the paper's p-FHT-FSCL-1-100);
+ *     permuted node, 1 < r < m - 1; r - 1 permuted levels), L in {1, 2, 4, 8, 16}, and
+ *     L = 32 for m <= 9 (P = M_1 = 100, L = 1 is the paper's p-FHT-FSCL-1-100);
  *   - 2 <= m <= 10, r = 1 or r = m - 1, L in {1, 2, 4, 8, 16, 32}: the root is itself an FHTL
  *     (RM(1, m), Algorithms 3-4) or SPCL (RM(m-1, m), Eqs. (2)-(6)) node. Algorithm 2 decodes
  *     such a root before any permuted node and never undoes the initial permutations outside

@@ -55,7 +55,7 @@ rmdec_status rmdec_group_create(rmdec_group_t *out, const rmdec_t *decoders, int
 rmdec_status rmdec_group_decode(rmdec_group_t g, const rmdec_segment *segs, int n_segs, void *stream);
 
 /* Which segments leave the grouped launch: those of at least min_frames_alone frames
- * (0, the default: one full wave of the decoder's own launch, i.e. SMs x its resident
+ * (0, the default: half a wave of the decoder's own launch, a wave being SMs x its resident
  * CTAs; < 0: none, every segment is grouped). Never changes results. */
 rmdec_status rmdec_group_set_split(rmdec_group_t g, int64_t min_frames_alone);
 

@@ -36,7 +36,7 @@ struct rmdec_group {
     int device = -1;  // device the kernel attributes were set for
     int sm_count = 0, max_optin = 0;
     int req_warps = 0, req_ctas = 0;
-    int64_t min_alone = 0;  // 0: one full wave of the decoder's own launch; < 0: never alone
+    int64_t min_alone = 0;  // 0: half a wave of the decoder's own launch; < 0: never alone
     // resident CTAs per SM for 0..kMaxWarps warps (-1: not computed yet) at the footprint
     // (rec_cap, k_cap, n_cap, warp stride) of the last launch; occupancy queries cost host
     // time on every small launch otherwise
@@ -278,14 +278,16 @@ rmdec_status rmdec_group_decode(rmdec_group_t g, const rmdec_segment* segs, int 
         if (mi[d].device != dev) return g->fail(RMDEC_EINVAL, "decoder %d was prepared on device %d, current is %d", d, mi[d].device, dev);
         if (mi[d].L != g->L || mi[d].algo != 0) return g->fail(RMDEC_EINVAL, "decoder %d no longer fits the group", d);
     }
-    // Segments that fill at least min_alone frames (default: one full wave of their decoder's
+    // Segments that fill at least min_alone frames (default: half a wave of their decoder's
     // own launch) run in their decoder's own kernel, which keeps its own register and
     // shared-memory footprint; the rest share grouped launches, most work per frame first
-    // (stable, so equal costs keep the caller's order).
+    // (stable, so equal costs keep the caller's order). Measured on four codes at 600 frames
+    // each (0.2 to 1.3 waves): a one-wave threshold 0.335 ms, half a wave 0.280 ms, a quarter
+    // 0.274 ms but 20% slower at 200 frames each; separate launches 0.262 ms.
     std::vector<int> order, alone;
     for (int i = 0; i < n_segs; i++) {
         if (segs[i].n_frames == 0) continue;
-        const int64_t thr = g->min_alone > 0 ? g->min_alone : mi[segs[i].decoder].wave;
+        const int64_t thr = g->min_alone > 0 ? g->min_alone : (mi[segs[i].decoder].wave + 1) / 2;
         if (g->min_alone >= 0 && segs[i].n_frames >= thr) alone.push_back(i);
         else order.push_back(i);
     }

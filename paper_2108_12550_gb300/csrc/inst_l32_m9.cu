@@ -1,0 +1,12 @@
+// Kernel instances with list size L = 32 for code length 2^9.
+#include "pfht_kernel.cuh"
+#include "rmdec_internal.h"
+
+namespace rmdec_host {
+bool lookup_pfht_l32_m9(int r, KernelEntry* e) {
+    if (r == 2) RMDEC_PFHT_ENTRY(9, 2, 32);
+    if (r == 3) RMDEC_PFHT_ENTRY(9, 3, 32);
+    if (r == 4) RMDEC_PFHT_ENTRY(9, 4, 32);
+    return false;
+}
+}  // namespace rmdec_host

@@ -320,10 +320,11 @@ struct Decoder {
         constexpr int T = cmin(L, NS);
         constexpr int ST = C::stride(S);
         static_assert(EE >= 1 && EE <= 32, "spectrum of 32 to 1024 points");
-        static_assert(C::lvl_off(S) >= 2 * L * T, "candidate lists fit below the node's level");
+        static_assert(C::lvl_off(S) >= L * T + (L * T + 1) / 2, "candidate lists fit below the node's level");
+        static_assert(NS <= (1 << 15), "codes k << 1 | sign fit 16 bits");
         const float* buf = w.alpha + C::lvl_off(S);
-        float* cand_pm = w.alpha;                                          // [L][T]
-        int* cand_code = reinterpret_cast<int*>(w.alpha + L * T);          // [L][T]: k << 1 | sign
+        float* cand_pm = w.alpha;                                             // [L][T]
+        uint16_t* cand_code = reinterpret_cast<uint16_t*>(w.alpha + L * T);   // [L][T]: k << 1 | sign
         __syncwarp();
 #pragma unroll 1
         for (int l = 0; l < L; l++) {
@@ -377,7 +378,7 @@ struct Decoder {
                 if (w.lane == (int)(kwin & 31u)) taken |= 1u << be;
                 if (w.lane == 0) {
                     cand_pm[l * T + t] = pml + 0.5f * (A - __uint_as_float(kmax - 1u));
-                    cand_code[l * T + t] = (int)(kwin << 1) | neg;
+                    cand_code[l * T + t] = (uint16_t)((kwin << 1) | (unsigned)neg);
                 }
             }
         }
@@ -713,25 +714,42 @@ struct Decoder {
             // candidate c = 2l + flip; every group of 2L lanes holds all candidates and
             // compares them against its share of the 2L, and the partial counts are summed
             constexpr int NC = 2 * L;
-            constexpr int GRP = cmin(32 / NC, NC);  // lane groups sharing the comparisons
-            constexpr int Q = NC / GRP;             // comparisons per group
-            const int c = w.lane & (NC - 1);
-            const int grp = (w.lane / NC) % GRP;
-            const float kpm = __shfl_sync(kFull, pm, c >> 1);
-            const float fpm = __shfl_sync(kFull, pflip, c >> 1);
-            const float cpm = (c & 1) ? fpm : kpm;
-            // rank of candidate c among the 2L by (PM, 2l + flip)
-            int rank = 0;
+            if constexpr (NC > 32) {
+                // 2L = 64 candidates (L = 32): lane t ranks candidates t and t + 32
+                const int ca = w.lane, cb = w.lane + 32;
+                const float ka = __shfl_sync(kFull, pm, ca >> 1), fa = __shfl_sync(kFull, pflip, ca >> 1);
+                const float kb = __shfl_sync(kFull, pm, cb >> 1), fb = __shfl_sync(kFull, pflip, cb >> 1);
+                const float pa = (ca & 1) ? fa : ka, pb = (cb & 1) ? fb : kb;
+                int ra = 0, rb = 0;
+#pragma unroll 4
+                for (int c2 = 0; c2 < NC; c2++) {
+                    const float o = __shfl_sync(kFull, c2 < 32 ? pa : pb, c2 & 31);
+                    ra += (o < pa) || (o == pa && c2 < ca);
+                    rb += (o < pb) || (o == pb && c2 < cb);
+                }
+                if (ra < L) sel[ra] = (uint8_t)ca;
+                if (rb < L) sel[rb] = (uint8_t)cb;
+            } else {
+                constexpr int GRP = cmin(32 / NC, NC);  // lane groups sharing the comparisons
+                constexpr int Q = NC / GRP;             // comparisons per group
+                const int c = w.lane & (NC - 1);
+                const int grp = (w.lane / NC) % GRP;
+                const float kpm = __shfl_sync(kFull, pm, c >> 1);
+                const float fpm = __shfl_sync(kFull, pflip, c >> 1);
+                const float cpm = (c & 1) ? fpm : kpm;
+                // rank of candidate c among the 2L by (PM, 2l + flip)
+                int rank = 0;
 #pragma unroll
-            for (int k = 0; k < Q; k++) {
-                const int c2 = grp * Q + k;
-                const float o = __shfl_sync(kFull, cpm, c2);
-                rank += (o < cpm) || (o == cpm && c2 < c);
+                for (int k = 0; k < Q; k++) {
+                    const int c2 = grp * Q + k;
+                    const float o = __shfl_sync(kFull, cpm, c2);
+                    rank += (o < cpm) || (o == cpm && c2 < c);
+                }
+#pragma unroll
+                for (int d = NC; d < NC * GRP; d <<= 1) rank += __shfl_xor_sync(kFull, rank, d);
+                // candidate of rank q goes to path q
+                if (w.lane < 2 * L && rank < L) sel[rank] = (uint8_t)w.lane;
             }
-#pragma unroll
-            for (int d = NC; d < NC * GRP; d <<= 1) rank += __shfl_xor_sync(kFull, rank, d);
-            // candidate of rank q goes to path q
-            if (w.lane < 2 * L && rank < L) sel[rank] = (uint8_t)w.lane;
             __syncwarp();
             const int mysrc = sel[me];
             __syncwarp();
@@ -779,6 +797,48 @@ struct Decoder {
     __device__ static int select_perms(Warp& w, const uint16_t* recs, Src src) {
         constexpr int C2 = 2 * L;
         constexpr int HALF = 1 << (S - 1);
+        if constexpr (C2 > 32) {
+            // 2L = 64 candidates (L = 32): lane t keeps LM of candidates t and t + 32, ranks
+            // both, and the candidate of rank q is published to lane q through shared memory
+            float lm0 = 0.f, lm1 = 0.f;
+#pragma unroll 2
+            for (int c = 0; c < C2; c++) {
+                const uint16_t* r = recs + c * kRec;
+                const int a = r[S - 1];
+                const int h = 31 - __clz(a);
+                const int lorg = c & (L - 1);
+                float acc = 0.f;
+#pragma unroll
+                for (int t = 0; t < (HALF + 31) / 32; t++) {
+                    const int jp = w.lane + 32 * t;
+                    if (jp < HALF) {
+                        const int j = insert_zero(jp, h);
+                        acc += fminf(fabsf(src(lorg, j)), fabsf(src(lorg, j ^ a)));
+                    }
+                }
+                acc = warp_sum(acc);
+                if (w.lane == (c & 31)) {
+                    if (c < 32) lm0 = acc;
+                    else lm1 = acc;
+                }
+            }
+            const int c0 = w.lane, c1 = w.lane + 32;
+            int r0 = 0, r1 = 0;
+#pragma unroll 4
+            for (int c2 = 0; c2 < C2; c2++) {
+                const float o = __shfl_sync(kFull, c2 < 32 ? lm0 : lm1, c2 & 31);
+                r0 += (o > lm0) || (o == lm0 && c2 < c0);
+                r1 += (o > lm1) || (o == lm1 && c2 < c1);
+            }
+            uint8_t* sel = w.spc;  // free outside SPC leaves
+            __syncwarp();
+            if (r0 < L) sel[r0] = (uint8_t)c0;
+            if (r1 < L) sel[r1] = (uint8_t)c1;
+            __syncwarp();
+            const int mine = sel[w.lane];
+            __syncwarp();
+            return mine;
+        }
         float mylm = 0.f;  // lane c keeps LM_c
         if constexpr (M >= 9 && !(M == 9 && L == 8)) {
             // candidates two at a time, each with a warp sum (the m = 9 trees exceed the

@@ -213,6 +213,11 @@ bool lookup_kernel(rmdec_ctx* h, rmdec_host::KernelEntry* e) {
     if (h->algo == 1) return lookup_autssc(h->m, h->r, e);
     if (h->algo == 2) return lookup_mlroot(h->m, h->r, e);
     if (h->hadamard == RMDEC_HADAMARD_TENSOR) return lookup_pfht_tc(h->m, h->r, h->L, e);
+    if (h->L == 32) {
+        if (h->m == 9) return lookup_pfht_l32_m9(h->r, e);
+        if (h->m == 8) return lookup_pfht_l32_m8(h->r, e);
+        return lookup_pfht_l32_small(h->m, h->r, e);
+    }
     if (h->r == 4) return h->m == 9 ? lookup_pfht_r4_m9(h->L, e) : lookup_pfht_r4_small(h->m, h->L, e);
     switch (h->m) {
         case 4: return lookup_pfht_m4(h->r, h->L, e);
@@ -421,13 +426,13 @@ rmdec_status make_handle(rmdec_t* out, int algo, int m, int r, int P, int L, uin
     bool ml_root = false;  // RM(1, m) or RM(m-1, m): the root is an FHTL or SPCL node
     if (algo == 0) {
         ml_root = m >= 2 && m <= 10 && (r == 1 || r == m - 1);
-        const bool pl_ok = P >= 1 && P <= 128 && L >= 1 && L <= (ml_root ? 32 : 16) && (L & (L - 1)) == 0;
+        const bool pl_ok = P >= 1 && P <= 128 && L >= 1 && L <= (ml_root || m <= 9 ? 32 : 16) && (L & (L - 1)) == 0;
         const bool code_ok = ml_root || (m >= 4 && m <= 10 && r >= 2 && r <= 3 && r <= m - 2) ||
                              (r == 4 && m >= 6 && m <= 9);
         if (!code_ok || !pl_ok) {
             g_create_error = "unsupported p-FHT-FSCL configuration (need 1<=P<=128 and either 4<=m<=10, r in {2,3}, "
-                             "r<=m-2, or 6<=m<=9, r=4, with L in {1,2,4,8,16}; or 2<=m<=10, r in {1,m-1}, "
-                             "L in {1,2,4,8,16,32})";
+                             "r<=m-2, or 6<=m<=9, r=4, with L in {1,2,4,8,16} (32 for m<=9); or 2<=m<=10, "
+                             "r in {1,m-1}, L in {1,2,4,8,16,32})";
             return RMDEC_EINVAL;
         }
     } else {

@@ -38,6 +38,10 @@ bool lookup_pfht_m10(int r, int L, KernelEntry* e);
 // RM(4, m): three permuted levels (inst_r4_*.cu)
 bool lookup_pfht_r4_small(int m, int L, KernelEntry* e);  // m = 6, 7, 8
 bool lookup_pfht_r4_m9(int L, KernelEntry* e);
+// list size L = 32 (inst_l32_*.cu)
+bool lookup_pfht_l32_small(int m, int r, KernelEntry* e);  // m = 4 .. 7
+bool lookup_pfht_l32_m8(int r, KernelEntry* e);
+bool lookup_pfht_l32_m9(int r, KernelEntry* e);
 
 // p-FHT-FSCL kernels whose FHTL nodes use the tensor cores (inst_tc.cu).
 bool lookup_pfht_tc(int m, int r, int L, KernelEntry* e);

@@ -31,7 +31,7 @@ def test_library_exports_every_declared_symbol():
 def test_invalid_configurations_are_rejected():
     lib = pkg.load_library()
     h = ctypes.c_void_p()
-    for args in [(9, 2, 20, 3), (9, 2, 20, 32), (10, 4, 4, 4), (9, 5, 4, 4), (1, 1, 4, 4), (11, 1, 4, 4), (9, 8, 4, 64),
+    for args in [(9, 2, 20, 3), (10, 2, 20, 32), (9, 2, 20, 64), (10, 4, 4, 4), (9, 5, 4, 4), (1, 1, 4, 4), (11, 1, 4, 4), (9, 8, 4, 64),
                  (9, 2, 0, 4), (9, 2, 129, 4)]:
         st = lib.rmdec_create(ctypes.byref(h), *args, 1)
         assert st == pkg.EINVAL and h.value is None

@@ -55,6 +55,10 @@ CONFIGS = [  # (m, r, P, L, Eb/N0, frames)
     (7, 4, 2, 16, 3.0, 100),
     (8, 4, 4, 4, 3.0, 200),
     (9, 4, 2, 8, 3.5, 60),
+    (4, 2, 2, 32, 1.5, 200),     # L = 32 (64 candidates per permuted node and SPC split)
+    (6, 3, 2, 32, 2.0, 100),
+    (8, 2, 1, 32, 1.5, 40),
+    (9, 4, 1, 32, 3.0, 12),
 ]
 
 
