@@ -35,10 +35,10 @@ WORKLOADS = {
     "rm39_p16_l8": (9, 3, 16, 8, 4.0, 1 << 16),
 }
 METRIC = "frames/s RM(2,9) P=20 L=4 at FER~1e-4 Eb/N0; p50/p99 latency, mixed load"
-# DRAM bytes per frame of one ncu capture of pfht_kernel<9,2,4> (16,384 frames: 33,641,984 B
+# DRAM bytes per frame of one ncu capture of pfht_kernel<9,2,4> (16,384 frames: 33,641,728 B
 # read + 0 B written), valid only for the kernel code it was taken on (the prefix of
 # kernel_fingerprint())
-TRAFFIC = {"rm29_p20_l4": {"bytes_per_frame": (33641984 + 0) / 16384, "kernel_code_sha256": "83d53763ef4434f4"}}
+TRAFFIC = {"rm29_p20_l4": {"bytes_per_frame": (33641728 + 0) / 16384, "kernel_code_sha256": "4e5d0ffbfdf3aa35"}}
 LANES_PER_SM = 128  # INT32/FP32 lanes per SM: one ALU operation per lane per clock
 
 

@@ -93,7 +93,10 @@ def test_group_membership_is_validated_on_the_host():
     e = pkg.Decoder(10, 2, 2, 4)
     f = pkg.Decoder(8, 2, 1, 4, algo="fhtfscl")
     ok = pkg.Group([a, b, f])  # host-side only: no device work at creation
-    for bad in ([a, c], [a, s], [e], []):
+    r4 = pkg.Decoder(8, 4, 2, 4)
+    l32 = pkg.Decoder(7, 2, 2, 32)
+    root1 = pkg.Decoder(7, 1, 2, 4)
+    for bad in ([a, c], [a, s], [e], [], [r4], [l32], [root1]):
         with pytest.raises(pkg.RmdecError) as ei:
             pkg.Group(bad)
         assert ei.value.status == pkg.EINVAL
