@@ -502,6 +502,8 @@ def main():
     ap.add_argument("--streams", type=int, default=4, help="serving mix: server CUDA streams")
     ap.add_argument("--frames", type=int, default=0, help="frames per step (default per workload)")
     ap.add_argument("--dtype", default="f32", choices=["f32", "i8", "f16", "i16"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "warp", "path"],
+                    help="decoder kernel: warp per decoder, thread per path (RM(2, m <= 7)), or auto")
     ap.add_argument("--hadamard", default="shuffle", choices=["shuffle", "tensor"],
                     help="FHT of the FHTL nodes: FP32 butterflies or FP16 tensor-core products")
     ap.add_argument("--cpu-frames", type=int, default=1500, help="CPU-baseline sample size")
@@ -544,6 +546,8 @@ def main():
     dec = pkg.Decoder(m, r, P, L, perm_seed=1, dtype=args.dtype)
     if args.hadamard != "shuffle":
         dec.set_hadamard(args.hadamard)
+    if args.kernel != "auto":
+        dec.set_kernel(args.kernel)
     x = torch.from_numpy(llr_np).cuda()
     out = torch.empty((nf, dec.kw), dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -625,7 +629,7 @@ def main():
                    "ebn0_db": ebn0, "frames_per_step": nf, "l2": "inputs larger than L2 "
                    f"({llr_np.nbytes / 2**20:.0f} MiB of LLRs per step)", "parallelism": f"replicas{world}",
                    "launch": dict(zip(("warps_per_cta", "ctas_per_sm"), dec.get_tuning())),
-                   "hadamard": args.hadamard},
+                   "hadamard": args.hadamard, "kernel": args.kernel},
         "info_gbit_s": value * k / 1e9,
         "fer_of_timed_batch": fer,
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,

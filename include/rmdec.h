@@ -111,6 +111,23 @@ typedef enum {
 } rmdec_hadamard;
 rmdec_status rmdec_set_hadamard(rmdec_t h, rmdec_hadamard mode);
 
+/* Which kernel runs a p-FHT-FSCL decode (Algorithms 2-5; the same method either way).
+ * AUTO (default): PATH where it exists, else WARP.
+ * WARP: one warp per decoder, the L paths spread over its lanes and the tree's LLR buffers in
+ *   shared memory; every supported code.
+ * PATH: one thread per list path, the tree's LLRs in registers, the decoders of a frame in
+ *   one lane group; RM(2, m) with 4 <= m <= 7 and L in {1, 2, 4, 8}, FP32 butterflies
+ *   (RMDEC_EINVAL otherwise). Integer inputs decode identically under both; FP32 inputs may
+ *   differ where two FHTL candidates of one path round to the same FP32 metric (WARP then
+ *   prefers the smaller index, PATH the larger |c_k|). Decoders that run PATH decode their
+ *   segments of a grouped launch in their own launch (rmdec_group.h). */
+typedef enum {
+    RMDEC_KERNEL_AUTO = 0,
+    RMDEC_KERNEL_WARP = 1,
+    RMDEC_KERNEL_PATH = 2,
+} rmdec_kernel;
+rmdec_status rmdec_set_kernel(rmdec_t h, rmdec_kernel kernel);
+
 /* Number of uint16 permutation records the handle holds (11 uint16 per record:
  * [c_0 .. c_9, b] with c_t = A e_t; the record maps index i to b XOR sum_{t: i_t = 1} c_t).
  * p-FHT-FSCL layout: decoder-major, per decoder L initial records then (r-1) * 2L candidate
@@ -177,7 +194,8 @@ rmdec_status rmdec_submit(rmdec_t h, const void *llr_dev, int64_t n_frames, uint
 rmdec_status rmdec_poll(rmdec_t h, uint64_t ticket, int64_t timeout_us);
 
 /* Launch shape: warps per CTA (1..20, at most P; Aut-SSC handles use at most 4; the decoders
- * of a frame are split across a CTA's warps) and a cap on resident CTAs per SM (0 = the
+ * of a frame are split across a CTA's warps; path-per-thread kernels (rmdec_set_kernel) take
+ * 1..4 warps, each decoding its own frames) and a cap on resident CTAs per SM (0 = the
  * occupancy limit); 0 warps = the default: the most resident warps per SM, then warps that
  * split the P decoders evenly, then two or more decoders per warp and two or more CTAs per
  * SM, then the narrowest CTA; a launch of at most four waves of that shape takes the shape

@@ -52,6 +52,7 @@ def load_library():
         "rmdec_destroy": ([V], None),
         "rmdec_set_dtype": ([V, I], I),
         "rmdec_set_hadamard": ([V, I], I),
+        "rmdec_set_kernel": ([V, I], I),
         "rmdec_perm_count": ([V, ctypes.POINTER(I64)], I),
         "rmdec_get_perms": ([V, V, I64], I),
         "rmdec_set_perms": ([V, V, I64], I),
@@ -152,6 +153,12 @@ class Decoder:
         """'shuffle' (FP32 butterflies, default) or 'tensor' (FP16 tensor-core products)."""
         self._check(self._lib.rmdec_set_hadamard(self._h, {"shuffle": 0, "tensor": 1}[mode]))
         self.hadamard = mode
+
+    def set_kernel(self, kernel):
+        """'auto' (default), 'warp' (one warp per decoder) or 'path' (one thread per list path,
+        RM(2, m) with 4 <= m <= 7 and L <= 8)."""
+        self._check(self._lib.rmdec_set_kernel(self._h, {"auto": 0, "warp": 1, "path": 2}[kernel]))
+        self.kernel = kernel
 
     def perm_count(self):
         n = ctypes.c_int64()

@@ -1,0 +1,44 @@
+// Kernel instances of the path-per-thread decoder for RM(2, m), 4 <= m <= 7 (ppt_kernel.cuh).
+#include "ppt_kernel.cuh"
+#include "rmdec_internal.h"
+
+namespace rmdec_host {
+
+namespace {
+template <int M, int L>
+bool ppt_entry(int P, KernelEntry* e) {
+    using D = rmdec_dev::Ppt<M, L>;
+    const int fw = rmdec_dev::ppt_frame_lanes(M, L, P);
+    e->fn = reinterpret_cast<const void*>(&rmdec_dev::ppt_kernel<M, L>);
+    e->frames_per_warp = 32 / fw;
+    e->warp_bytes = e->frames_per_warp * D::N * 4 + 32;
+    e->nrec = 0;  // the maps sit in the fixed part
+    e->fixed_bytes = [](int P2, int K, int) {
+        return ((P2 * 2 * rmdec_dev::Ppt<M, L>::NREC * rmdec_dev::kRec * 2 + K * 2) + 15) / 16 * 16;
+    };
+    return true;
+}
+template <int M>
+bool ppt_case(int L, int P, KernelEntry* e) {
+    switch (L) {
+        case 1: return ppt_entry<M, 1>(P, e);
+        case 2: return ppt_entry<M, 2>(P, e);
+        case 4: return ppt_entry<M, 4>(P, e);
+        case 8: return ppt_entry<M, 8>(P, e);
+    }
+    return false;
+}
+}  // namespace
+
+bool lookup_pfht_ppt(int m, int r, int L, int P, KernelEntry* e) {
+    if (r != 2) return false;
+    switch (m) {
+        case 4: return ppt_case<4>(L, P, e);
+        case 5: return ppt_case<5>(L, P, e);
+        case 6: return ppt_case<6>(L, P, e);
+        case 7: return ppt_case<7>(L, P, e);
+    }
+    return false;
+}
+
+}  // namespace rmdec_host

@@ -1,0 +1,679 @@
+// p-FHT-FSCL-L-M for the short codes RM(2, m), 4 <= m <= 7, with one thread per list path.
+//
+// Method: Doan, Hashemi, Gross, arXiv 2108.12550 — Algorithm 2 (the root is the one permuted
+// node of an RM(2, m) tree: 2L candidate permutations ranked by the reliability metric LM),
+// Algorithms 3-4 with Eq. (8) (FHTL nodes RM(1, s)), Eqs. (2)-(6) (the SPCL node RM(2, 3)) and
+// Algorithm 5 (the best of P decoders).
+//
+// Execution model. The L paths of one decoder are L consecutive lanes of a warp; a lane keeps
+// its path's LLRs of every pending tree level, its Walsh-Hadamard spectra and its decided bits
+// in registers (at most 2^(m-1) + 2^(m-2) floats), so the tree's f/g steps and butterflies run
+// without shuffles or shared memory and every lane does useful work. Lists interact only at
+// the leaves: the survivors are chosen by shuffles among the decoder's L lanes, and a new path
+// copies its parent's pending LLRs with one shuffle per value. The decoders of a frame occupy
+// a group of FW consecutive lanes (FW = L x decoders per batch, a power of two); a warp
+// decodes 32 / FW frames at once, their LLRs staged in the warp's own shared memory, and runs
+// the P decoders of each frame in batches of FW / L.
+//
+// Results: integer-valued inputs decode bit-exactly as the warp-per-decoder kernel and the
+// integer oracle do (every operation is exact there). Sums (the metric LM, sum |alpha| of an
+// FHTL node) and butterflies take the warp-per-decoder kernel's association order. A path
+// offers its FHTL candidates in the order (|c_k| descending, k ascending); the survivors of a
+// leaf are the L smallest by (PM', path, k), PM' = PM + (sum|alpha| - |c_k|) / 2 in FP32.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_fp16.h>
+
+#include "pfht_kernel.cuh"
+
+namespace rmdec_dev {
+
+// Lanes per frame group: the decoders of one batch (L lanes each); at least N / 32 lanes, so
+// that a warp stages at most 32 N / FW <= 1024 LLRs (4 KB).
+__host__ __device__ constexpr int ppt_pow2_ceil(int x) { return x <= 1 ? 1 : 2 * ppt_pow2_ceil((x + 1) / 2); }
+__host__ __device__ inline int ppt_frame_lanes(int m, int L, int P) {
+    const int n32 = m >= 5 ? (1 << m) / 32 : 1;
+    int fw = ppt_pow2_ceil(P * L);
+    if (fw > 32) fw = 32;
+    if (fw < n32) fw = n32;
+    return fw;
+}
+
+// trailing zeros of 0 < n < 128 (folds to a constant for constant n, unlike a recursion)
+__host__ __device__ constexpr int ctz7(int n) {
+    return (n & 1) ? 0 : (n & 2) ? 1 : (n & 4) ? 2 : (n & 8) ? 3 : (n & 16) ? 4 : (n & 32) ? 5 : 6;
+}
+
+// Word `idx` (< NW <= 4) of a register array, by a multiplexer on the index bits (an equality
+// chain would be turned into a local-memory array by the compiler).
+template <int NW>
+__device__ __forceinline__ uint32_t pick_word(const uint32_t (&x)[NW], int idx) {
+    if constexpr (NW == 1) {
+        return x[0];
+    } else if constexpr (NW == 2) {
+        return (idx & 1) ? x[1] : x[0];
+    } else {
+        static_assert(NW == 4, "one to four words");
+        const uint32_t lo = (idx & 1) ? x[1] : x[0], hi = (idx & 1) ? x[3] : x[2];
+        return (idx & 2) ? hi : lo;
+    }
+}
+
+template <int M, int L>
+struct Ppt {
+    static constexpr int N = 1 << M;
+    static constexpr int H = N / 2;
+    static constexpr int NW = (N + 31) / 32;
+    static constexpr int NREC = 2 * L;  // root candidates per decoder (one permuted level)
+    static_assert(M >= 4 && M <= 7, "short codes");
+    static_assert(L == 1 || L == 2 || L == 4 || L == 8, "list size");
+
+    struct Ctx {
+        const float* y;         // the frame's LLRs (shared memory)
+        const uint16_t* rec;    // the decoder's 2L composed root records (shared memory)
+        uint8_t* sel;           // the warp's 32-byte selection scratch
+        int dbase;              // lane of the decoder's path 0
+        int l;                  // this lane's path
+        bool single;            // paths 1..L-1 start inactive (metric +inf)
+    };
+    struct Path {
+        float pm;
+        int rootc;         // root candidate (composed permutation) the path descends from
+        uint32_t x[NW];    // decided bits of the permuted word, span layout of the tree
+    };
+
+    // bit i of the decided word
+    __device__ __forceinline__ static unsigned bit(const Path& p, int i) { return (p.x[i >> 5] >> (i & 31)) & 1u; }
+
+    // Writes the NB bits `v` at span offset OFF (NB <= 32 and OFF a multiple of NB, or NB a
+    // multiple of 32 with v holding word `wd`).
+    template <int OFF, int NB>
+    __device__ __forceinline__ static void put_bits(Path& p, unsigned v) {
+        static_assert(NB <= 32 && OFF % NB == 0, "small span");
+        constexpr unsigned mask = (NB == 32 ? 0xffffffffu : ((1u << NB) - 1u)) << (OFF % 32);
+        p.x[OFF / 32] = (p.x[OFF / 32] & ~mask) | ((v << (OFF % 32)) & mask);
+    }
+
+    // x_v = (x_gamma ^ x_lambda, x_gamma) on the span [OFF, OFF + 2 HS) (Algorithm 2)
+    template <int OFF, int HS>
+    __device__ __forceinline__ static void combine(Path& p) {
+        if constexpr (HS >= 32) {
+#pragma unroll
+            for (int w = 0; w < HS / 32; w++) p.x[OFF / 32 + w] ^= p.x[(OFF + HS) / 32 + w];
+        } else {
+            constexpr unsigned mh = (1u << HS) - 1u;
+            p.x[OFF / 32] ^= ((p.x[OFF / 32] >> ((OFF % 32) + HS)) & mh) << (OFF % 32);
+        }
+    }
+
+    // New path (this lane) descends from path `par`: its root candidate, the pending LLRs
+    // `pend` (PC values) and the decided bits left of span offset OFF.
+    template <int OFF, int PC, int PA>
+    __device__ __forceinline__ static void list_step(const Ctx& c, Path& p, int par, float (&pend)[PA]) {
+        const int src = c.dbase + par;
+        p.rootc = __shfl_sync(kFull, p.rootc, src);
+#pragma unroll
+        for (int i = 0; i < PC; i++) pend[i] = __shfl_sync(kFull, pend[i], src);
+#pragma unroll
+        for (int w = 0; w < (OFF + 31) / 32; w++) p.x[w] = __shfl_sync(kFull, p.x[w], src);
+    }
+
+    // --------------------------------------------------------------- FHTL leaf ---
+    // RM(1, S) node at span offset OFF (Algorithms 3-4, Eq. (8)): spectrum c = H alpha, path
+    // candidates (k, sign of c_k) with PM' = PM + (sum|alpha| - |c_k|) / 2; the L best over the
+    // decoder's paths by (PM', path, k) survive. pend: the PC pending LLRs a new path copies.
+    template <int S, int OFF, int PC, int PA>
+    __device__ __forceinline__ static void fht_leaf(const Ctx& c, Path& p, float (&v)[1 << S], float (&pend)[PA]) {
+        constexpr int NS = 1 << S;
+        constexpr int T = cmin(L, NS);
+        static_assert(T == L, "every path offers L candidates");
+        // the warp-per-decoder kernel's lanes per path (G) and values per lane (E): sums and
+        // butterflies below associate as its lane and register steps do
+        constexpr int G = cmin(32 / L, NS);
+        constexpr int E = NS / G;
+        float A;
+        {
+            float tg[G];
+#pragma unroll
+            for (int g = 0; g < G; g++) {
+                float t[E];
+#pragma unroll
+                for (int e = 0; e < E; e++) t[e] = fabsf(v[g + G * e]);
+#pragma unroll
+                for (int h = E / 2; h >= 1; h >>= 1)
+#pragma unroll
+                    for (int e = 0; e < h; e++) t[e] += t[e + h];
+                tg[g] = t[0];
+            }
+#pragma unroll
+            for (int d = 1; d < G; d <<= 1)
+#pragma unroll
+                for (int g = 0; g < G; g += 2 * d) tg[g] += tg[g + d];
+            A = tg[0];
+        }
+        // butterflies (u, w) -> (u + w, u - w): index bits of e, then of g
+#pragma unroll
+        for (int h = 1; h < E; h <<= 1)
+#pragma unroll
+            for (int e = 0; e < E; e++)
+                if (!(e & h))
+#pragma unroll
+                    for (int g = 0; g < G; g++) {
+                        const float a = v[g + G * e], b = v[g + G * (e + h)];
+                        v[g + G * e] = a + b;
+                        v[g + G * (e + h)] = a - b;
+                    }
+#pragma unroll
+        for (int d = 1; d < G; d <<= 1)
+#pragma unroll
+            for (int g = 0; g < G; g++)
+                if (!(g & d))
+#pragma unroll
+                    for (int e = 0; e < E; e++) {
+                        const float a = v[g + G * e], b = v[(g | d) + G * e];
+                        v[g + G * e] = a + b;
+                        v[(g | d) + G * e] = a - b;
+                    }
+        // the path's T best candidates by (|c_k| descending, k ascending): a scan in k order
+        // inserts before the first entry of strictly smaller |c|; entries hold |c| (sentinel
+        // -1) and 2k + [c_k < 0]
+        float tv[T];
+        unsigned tk[T];
+#pragma unroll
+        for (int j = 0; j < T; j++) {
+            tv[j] = -1.f;
+            tk[j] = 2u * j;
+        }
+#pragma unroll
+        for (int k = 0; k < NS; k++) {
+            const float x = fabsf(v[k]);
+            const unsigned xk = 2u * k + (v[k] < 0.f ? 1u : 0u);
+            // the new list from the old one: entry j keeps, takes x, or takes entry j - 1
+            bool gt[T];
+#pragma unroll
+            for (int j = 0; j < T; j++) gt[j] = x > tv[j];
+            float ntv[T];
+            unsigned ntk[T];
+            ntv[0] = gt[0] ? x : tv[0];
+            ntk[0] = gt[0] ? xk : tk[0];
+#pragma unroll
+            for (int j = 1; j < T; j++) {
+                ntv[j] = gt[j - 1] ? tv[j - 1] : (gt[j] ? x : tv[j]);
+                ntk[j] = gt[j - 1] ? tk[j - 1] : (gt[j] ? xk : tk[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < T; j++) {
+                tv[j] = ntv[j];
+                tk[j] = ntk[j];
+            }
+        }
+        // keys (PM', path 2^(S+1) + 2k + sign) of the path's list, in ascending order
+        unsigned key[T], cid[T];
+#pragma unroll
+        for (int j = 0; j < T; j++) {
+            key[j] = ordered_bits(p.pm + 0.5f * (A - tv[j]));
+            cid[j] = ((unsigned)c.l << (S + 1)) | tk[j];
+        }
+        unsigned mkey = key[0], mcid = cid[0];
+        if constexpr (L > 1) {
+            // L rounds of the decoder-wide minimum of the lanes' heads; round q's winner
+            // becomes path q
+#pragma unroll
+            for (int q = 0; q < L; q++) {
+                unsigned bk = key[0], bc = cid[0];
+#pragma unroll
+                for (int d = 1; d < L; d <<= 1) {
+                    const unsigned ok = __shfl_xor_sync(kFull, bk, d);
+                    const unsigned oc = __shfl_xor_sync(kFull, bc, d);
+                    const bool take = ok < bk || (ok == bk && oc < bc);
+                    bk = take ? ok : bk;
+                    bc = take ? oc : bc;
+                }
+                if (c.l == q) {
+                    mkey = bk;
+                    mcid = bc;
+                }
+                if (q + 1 < L && cid[0] == bc) {  // the owner pops its head (ids are unique)
+#pragma unroll
+                    for (int j = 0; j + 1 < T; j++) {
+                        key[j] = key[j + 1];
+                        cid[j] = cid[j + 1];
+                    }
+                }
+            }
+        }
+        const int par = (int)(mcid >> (S + 1)) & (L - 1);
+        const int k = (int)(mcid >> 1) & (NS - 1);
+        const unsigned neg = mcid & 1u;
+        p.pm = ordered_float(mkey);
+        list_step<OFF, PC>(c, p, par, pend);
+        // decided bits x_j = <k, j> xor sign over the span
+        auto pattern = [&](int kk, int wd) {
+            unsigned pat = 0;
+#pragma unroll
+            for (int t = 0; t < 5; t++) {
+                const unsigned mt = t == 0 ? 0xAAAAAAAAu : t == 1 ? 0xCCCCCCCCu : t == 2 ? 0xF0F0F0F0u
+                                   : t == 3 ? 0xFF00FF00u : 0xFFFF0000u;
+                if (t < S && ((kk >> t) & 1)) pat ^= mt;
+            }
+            if ((__popc((unsigned)(kk >> 5) & (unsigned)wd) & 1) ^ neg) pat = ~pat;
+            return pat;
+        };
+        if constexpr (NS >= 32) {
+#pragma unroll
+            for (int wd = 0; wd < NS / 32; wd++) p.x[OFF / 32 + wd] = pattern(k, wd);
+        } else {
+            put_bits<OFF, NS>(p, pattern(k, 0));
+        }
+    }
+
+    // --------------------------------------------------------------- SPCL leaf ---
+    // RM(2, 3) node (Eqs. (2)-(6)): parity, PM += p |alpha_lrb|, then tau = min(L, 7) list
+    // splits on the next least reliable positions (flip cost |alpha_i| + (1-2p)|alpha_lrb|, each
+    // a 2L -> L selection by (PM, 2 path + flip)); the least reliable bit restores even parity.
+    template <int OFF>
+    __device__ __forceinline__ static void spc_leaf(const Ctx& c, Path& p, float (&a)[8]) {
+        constexpr int NS = 8;
+        constexpr int TAU = cmin(L, NS - 1);
+        // reliability order (|alpha|, position) ascending: Batcher's odd-even merge sort network
+        float sv[NS];
+        int sp[NS];
+#pragma unroll
+        for (int i = 0; i < NS; i++) {
+            sv[i] = fabsf(a[i]);
+            sp[i] = i;
+        }
+        auto cx = [&](int i, int j) {  // order entries i < j
+            const bool sw = sv[j] < sv[i] || (sv[j] == sv[i] && sp[j] < sp[i]);
+            const float tv = sv[i];
+            const int tp = sp[i];
+            sv[i] = sw ? sv[j] : sv[i];
+            sp[i] = sw ? sp[j] : sp[i];
+            sv[j] = sw ? tv : sv[j];
+            sp[j] = sw ? tp : sp[j];
+        };
+        cx(0, 1); cx(2, 3); cx(4, 5); cx(6, 7);
+        cx(0, 2); cx(1, 3); cx(4, 6); cx(5, 7);
+        cx(1, 2); cx(5, 6);
+        cx(0, 4); cx(1, 5); cx(2, 6); cx(3, 7);
+        cx(2, 4); cx(3, 5);
+        cx(1, 2); cx(3, 4); cx(5, 6);
+        const int o0 = sp[0];
+        const float lrb = sv[0];
+        float rel[TAU];
+        int pos[TAU];
+#pragma unroll
+        for (int t = 0; t < TAU; t++) {
+            rel[t] = sv[1 + t];
+            pos[t] = sp[1 + t];
+        }
+        unsigned hd = 0;
+#pragma unroll
+        for (int i = 0; i < NS; i++) hd |= (a[i] < 0.f ? 1u : 0u) << i;
+        int par = __popc(hd) & 1;
+        float pm = p.pm + (par ? lrb : 0.f);  // Eq. (3)
+        unsigned flip = 0;
+        int orig = c.l;
+#pragma unroll 1
+        for (int t = 1; t <= TAU; t++) {
+            // the split position and the LRB belong to the path's SPC-entry ancestor `orig`
+            const int so = c.dbase + orig;
+            const float r_o = __shfl_sync(kFull, rel[0], so);
+            const int itp = __shfl_sync(kFull, pos[0], so);
+            const float lrb_o = __shfl_sync(kFull, lrb, so);
+            const float pflip = pm + r_o + (par ? -lrb_o : lrb_o);  // Eq. (4)
+            // ranks of this path's candidates 2l (keep) and 2l + 1 (flip) among the 2L
+            int rk = 0, rf = 0;
+#pragma unroll
+            for (int l2 = 0; l2 < L; l2++) {
+                const float k2 = __shfl_sync(kFull, pm, c.dbase + l2);
+                const float f2 = __shfl_sync(kFull, pflip, c.dbase + l2);
+                rk += (k2 < pm) || (k2 == pm && l2 < c.l);
+                rk += (f2 < pm) || (f2 == pm && l2 < c.l);
+                rf += (k2 < pflip) || (k2 == pflip && l2 <= c.l);
+                rf += (f2 < pflip) || (f2 == pflip && l2 < c.l);
+            }
+            // the candidate of rank q becomes path q
+            if (rk < L) c.sel[c.dbase + rk] = (uint8_t)(2 * c.l);
+            if (rf < L) c.sel[c.dbase + rf] = (uint8_t)(2 * c.l + 1);
+            __syncwarp();
+            const int mysrc = c.sel[c.dbase + c.l];
+            __syncwarp();
+            const int sl = c.dbase + ((mysrc >> 1) & (L - 1));
+            const bool fl = mysrc & 1;
+            const float n_kpm = __shfl_sync(kFull, pm, sl);
+            const float n_fpm = __shfl_sync(kFull, pflip, sl);
+            const unsigned packed = __shfl_sync(kFull, (unsigned)orig | ((unsigned)par << 8) | ((unsigned)itp << 16), sl);
+            const unsigned n_flip = __shfl_sync(kFull, flip, sl);
+            pm = fl ? n_fpm : n_kpm;
+            orig = (int)(packed & 0xffu) & (L - 1);
+            const int n_it = (int)(packed >> 16) & (NS - 1);
+            flip = fl ? (n_flip ^ (1u << n_it)) : n_flip;  // Eq. (5)
+            par = (int)((packed >> 8) & 1u) ^ (fl ? 1 : 0);
+#pragma unroll
+            for (int k = 0; k + 1 < TAU; k++) {
+                rel[k] = rel[k + 1];
+                pos[k] = pos[k + 1];
+            }
+        }
+        const int so = c.dbase + orig;
+        const unsigned hd_o = __shfl_sync(kFull, hd, so);
+        const int lo0 = __shfl_sync(kFull, o0, so) & (NS - 1);
+        unsigned x = ((hd_o ^ flip) & 0xffu) & ~(1u << lo0);
+        x |= (unsigned)(__popc(x) & 1) << lo0;  // Eq. (6)
+        p.pm = pm;
+        float none[1];
+        list_step<OFF, 0>(c, p, orig, none);
+        put_bits<OFF, NS>(p, x);
+    }
+
+    // ------------------------------------------------------------- tree walk ---
+    // RM(2, S) node off the root (not permuted), LLRs `a`, at span offset OFF
+    template <int S, int OFF>
+    __device__ __forceinline__ static void node2(const Ctx& c, Path& p, float (&a)[1 << S]) {
+        if constexpr (S == 3) {
+            spc_leaf<OFF>(c, p, a);
+        } else {
+            constexpr int HS = 1 << (S - 1);
+            float ch[HS];
+#pragma unroll
+            for (int i = 0; i < HS; i++) ch[i] = fminsum(a[i], a[i + HS]);
+            fht_leaf<S - 1, OFF, 1 << S>(c, p, ch, a);
+#pragma unroll
+            for (int i = 0; i < HS; i++) ch[i] = g_fn(a[i], a[i + HS], bit(p, OFF + i));
+            node2<S - 1, OFF + HS>(c, p, ch);
+            combine<OFF, HS>(p);
+        }
+    }
+
+    // The root's 2L candidates (Algorithm 2's permutation decoding): candidate c permutes y
+    // through its composed record; LM_c = sum over the pairs {j, j ^ a} of min(|y_j|, |y_{j^a}|),
+    // a the image of the top index bit, summed as the warp-per-decoder kernel's lanes and warp
+    // reduction do. Returns this path's candidate: the one of rank l by (LM desc, c asc).
+    __device__ __forceinline__ static int select_root(const Ctx& c) {
+        constexpr int V = H < 32 ? H : 32;  // lanes of that kernel holding pairs
+        float lm[2];
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            const uint16_t* r = c.rec + (c.l + q * L) * kRec;
+            const int a = r[M - 1];
+            const int hm = ~((1 << (31 - __clz(a))) - 1);  // index bits at and above bit msb(a)
+            float acc[V];
+#pragma unroll
+            for (int lv = 0; lv < V; lv++) {
+                float s = 0.f;
+#pragma unroll
+                for (int t = 0; t < (H + 31) / 32; t++) {
+                    const int jp = lv + 32 * t;  // the pair's representative: bit msb(a) clear
+                    const int j = jp + (jp & hm);
+                    s += fminf(fabsf(c.y[j]), fabsf(c.y[j ^ a]));
+                }
+                acc[lv] = s;
+            }
+#pragma unroll
+            for (int d = 16; d >= 1; d >>= 1)
+#pragma unroll
+                for (int lv = 0; lv < d; lv++)
+                    if (lv + d < V) acc[lv] += acc[lv + d];
+            lm[q] = acc[0];
+        }
+        if constexpr (L == 1) {
+            return (lm[1] > lm[0]) ? 1 : 0;
+        } else {
+            int rk[2] = {0, 0};
+#pragma unroll
+            for (int l2 = 0; l2 < L; l2++) {
+#pragma unroll
+                for (int q2 = 0; q2 < 2; q2++) {
+                    const float o = __shfl_sync(kFull, lm[q2], c.dbase + l2);
+                    const int c2 = l2 + q2 * L;
+#pragma unroll
+                    for (int q = 0; q < 2; q++) {
+                        const int cc = c.l + q * L;
+                        rk[q] += (o > lm[q]) || (o == lm[q] && c2 < cc);
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 2; q++)
+                if (rk[q] < L) c.sel[c.dbase + rk[q]] = (uint8_t)(c.l + q * L);
+            __syncwarp();
+            const int mine = c.sel[c.dbase + c.l] & (2 * L - 1);
+            __syncwarp();
+            return mine;
+        }
+    }
+
+    // One decoder (Algorithm 2 from the root). Path 0 ends as the decoder's best path, its
+    // bits combined below the root.
+    __device__ __forceinline__ static void run(const Ctx& c, Path& p) {
+        p.rootc = select_root(c);
+        p.pm = (c.single && (p.rootc & (L - 1)) != 0) ? __int_as_float(0x7f800000) : 0.f;
+#pragma unroll
+        for (int w = 0; w < NW; w++) p.x[w] = 0;
+        float a[H];
+        int col[M - 1];
+        int sb, sa;
+        auto load_rec = [&]() {
+            const uint16_t* r = c.rec + p.rootc * kRec;
+#pragma unroll
+            for (int t = 0; t < M - 1; t++) col[t] = r[t];
+            sa = r[M - 1];
+            sb = r[10];
+        };
+        // f: left child RM(1, m-1) from y through the path's root permutation, positions in
+        // Gray-code order (one XOR per position)
+        load_rec();
+        {
+            int s = sb;
+#pragma unroll
+            for (int n = 0; n < H; n++) {
+                if (n) s ^= col[ctz7(n)];
+                const int i = n ^ (n >> 1);
+                a[i] = fminsum(c.y[s], c.y[s ^ sa]);
+            }
+        }
+        float none[1];
+        fht_leaf<M - 1, 0, 0>(c, p, a, none);
+        // g: right child RM(2, m-1) from y through the (possibly new) path's permutation
+        load_rec();
+        {
+            int s = sb;
+#pragma unroll
+            for (int n = 0; n < H; n++) {
+                if (n) s ^= col[ctz7(n)];
+                const int i = n ^ (n >> 1);
+                a[i] = g_fn(c.y[s], c.y[s ^ sa], bit(p, i));
+            }
+        }
+        node2<M - 1, H>(c, p, a);
+    }
+};
+
+// Decodes the frames of the job, one warp per 32 / FW frames (see Ppt).
+template <int M, int L>
+__global__ void __launch_bounds__(128, (M >= 6 ? 3 : 4)) ppt_kernel(LaunchArgs a) {
+    using D = Ppt<M, L>;
+    constexpr int N = D::N, NW = D::NW, NREC = D::NREC;
+    constexpr int K = 1 + M + M * (M - 1) / 2;  // information bits of RM(2, m)
+    static_assert(K <= 32, "one information word");
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int FW = ppt_frame_lanes(M, L, a.P);
+    const int FPW = 32 / FW;
+    const int W = blockDim.x >> 5;
+    // shared memory: the P decoders' maps and inverse maps as in the device table, the
+    // information positions, then per warp its frames' LLRs and a selection scratch
+    const int rec_elems = a.P * 2 * NREC * kRec;
+    uint16_t* s_rec = reinterpret_cast<uint16_t*>(smem);
+    uint16_t* s_info = s_rec + rec_elems;
+    const int tables = ((rec_elems * 2 + K * 2) + 15) / 16 * 16;
+    const int warp_bytes = FPW * N * 4 + 32;
+    for (int i = threadIdx.x; i < rec_elems; i += blockDim.x) s_rec[i] = a.recs[i];
+    for (int i = threadIdx.x; i < K; i += blockDim.x) s_info[i] = a.info[i];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* s_y = reinterpret_cast<float*>(smem + tables + warp * warp_bytes);
+    uint8_t* s_sel = smem + tables + warp * warp_bytes + FPW * N * 4;
+    const int grp = lane / FW, j = lane % FW, gbase = grp * FW;
+    const int DPB = FW / L;  // decoders per batch
+    const int ds = j / L;
+    typename D::Ctx c;
+    c.y = s_y + grp * N;
+    c.sel = s_sel;
+    c.dbase = gbase + ds * L;
+    c.l = j % L;
+    c.single = a.single_start != 0;
+    const unsigned gmask = FW == 32 ? 0xffffffffu : ((1u << FW) - 1u);
+    const size_t eb = a.dtype == IN_F32 ? 4 : (a.dtype == IN_I8 ? 1 : 2);
+    const int64_t nblk = (a.n_frames + FPW - 1) / FPW;
+    for (int64_t fb = (int64_t)blockIdx.x * W + warp; fb < nblk; fb += (int64_t)gridDim.x * W) {
+        const int64_t f0 = fb * FPW;
+        // the FPW frames' LLRs (contiguous), 16 bytes per load, widened to float
+        {
+            const int chunks = (int)(FPW * N * eb / 16);
+            const int per = (int)(16 / eb);  // values per chunk
+            const uint4* src = reinterpret_cast<const uint4*>(static_cast<const uint8_t*>(a.llr) + f0 * N * eb);
+            __syncwarp();
+            for (int i = lane; i < chunks; i += 32) {
+                if (f0 + (int64_t)(i * per) / N >= a.n_frames) continue;
+                const uint4 q = src[i];
+                const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
+                float4* dst = reinterpret_cast<float4*>(s_y + i * per);
+                if (a.dtype == IN_F32) {
+                    dst[0] = make_float4(__uint_as_float(wv[0]), __uint_as_float(wv[1]), __uint_as_float(wv[2]),
+                                         __uint_as_float(wv[3]));
+                } else if (a.dtype == IN_I8) {
+#pragma unroll
+                    for (int b = 0; b < 4; b++)
+                        dst[b] = make_float4((float)((int32_t)(wv[b] << 24) >> 24), (float)((int32_t)(wv[b] << 16) >> 24),
+                                             (float)((int32_t)(wv[b] << 8) >> 24), (float)((int32_t)wv[b] >> 24));
+                } else if (a.dtype == IN_F16) {
+                    auto h = [](uint32_t w, int hi) {
+                        return __half2float(__ushort_as_half((unsigned short)(hi ? (w >> 16) : (w & 0xffffu))));
+                    };
+#pragma unroll
+                    for (int b = 0; b < 2; b++)
+                        dst[b] = make_float4(h(wv[2 * b], 0), h(wv[2 * b], 1), h(wv[2 * b + 1], 0), h(wv[2 * b + 1], 1));
+                } else {
+                    float v8[8];
+#pragma unroll
+                    for (int b = 0; b < 4; b++) {
+                        v8[2 * b] = fminf(fmaxf((float)((int32_t)(wv[b] << 16) >> 16), -a.qclamp), a.qclamp);
+                        v8[2 * b + 1] = fminf(fmaxf((float)((int32_t)wv[b] >> 16), -a.qclamp), a.qclamp);
+                    }
+                    dst[0] = make_float4(v8[0], v8[1], v8[2], v8[3]);
+                    dst[1] = make_float4(v8[4], v8[5], v8[6], v8[7]);
+                }
+            }
+            __syncwarp();
+        }
+        const int64_t f = f0 + grp;
+        unsigned best_key = 0xffffffffu;
+        int best_d = 0;
+        float best_pm = 0.f;
+        uint32_t cw[NW];
+#pragma unroll
+        for (int w = 0; w < NW; w++) cw[w] = 0;
+        for (int b0 = 0; b0 < a.P; b0 += DPB) {
+            const int d = b0 + ds;
+            const bool dvalid = d < a.P;
+            const int dd = dvalid ? d : a.P - 1;
+            c.rec = s_rec + dd * 2 * NREC * kRec;
+            typename D::Path p;
+            D::run(c, p);
+            // Algorithm 5 over the batch: the smallest metric (NaN last), earlier decoders
+            // first; lanes of path 0 hold each decoder's best path
+            const float v = p.pm == p.pm ? p.pm : __int_as_float(0x7f800000);
+            unsigned bk = dvalid ? ordered_bits(v) : 0xffffffffu;
+            unsigned bd = (unsigned)ds;
+            for (int dl = L; dl < FW; dl <<= 1) {
+                const unsigned ok = __shfl_xor_sync(kFull, bk, dl);
+                const unsigned od = __shfl_xor_sync(kFull, bd, dl);
+                const bool take = ok < bk || (ok == bk && od < bd);
+                bk = take ? ok : bk;
+                bd = take ? od : bd;
+            }
+            bk = __shfl_sync(kFull, bk, gbase);
+            bd = __shfl_sync(kFull, bd, gbase);
+            const int wl = gbase + (int)bd * L;
+            uint32_t xw[NW];
+#pragma unroll
+            for (int w = 0; w < NW; w++) xw[w] = __shfl_sync(kFull, p.x[w], wl);
+            const int wc = __shfl_sync(kFull, p.rootc, wl);
+            const float wpm = __shfl_sync(kFull, p.pm, wl);
+            // root combine, then x[sigma(i)] = x'[i]: bit q of the codeword is bit sigma^-1(q)
+            // of the permuted word, read through the stored inverse map; lane j of the group
+            // takes positions j + FW t (every lane of the warp runs this: the ballots need them)
+            if constexpr (D::H >= 32) {
+#pragma unroll
+                for (int w = 0; w < NW / 2; w++) xw[w] ^= xw[w + NW / 2];
+            } else {
+                xw[0] ^= (xw[0] >> D::H) & ((1u << D::H) - 1u);
+            }
+            const int dw = b0 + (int)bd;
+            const uint16_t* ri = s_rec + (dw * 2 + 1) * NREC * kRec + wc * kRec;
+            uint32_t nw[NW];
+#pragma unroll
+            for (int w = 0; w < NW; w++) {  // word w: FW positions per ballot
+                nw[w] = 0;
+                for (int o = 0; o < 32 && 32 * w + o < N; o += FW) {
+                    const int q = 32 * w + o + j;
+                    unsigned b = 0;
+                    if (q < N) {
+                        const int sp = ga_apply(ri, M, q);
+                        b = (pick_word(xw, sp >> 5) >> (sp & 31)) & 1u;
+                    }
+                    nw[w] |= ((__ballot_sync(kFull, b) >> gbase) & gmask) << o;
+                }
+            }
+            if (bk < best_key || b0 == 0) {  // strict: earlier decoders win ties
+#pragma unroll
+                for (int w = 0; w < NW; w++) cw[w] = nw[w];
+                best_key = bk;
+                best_d = dw;
+                best_pm = wpm == wpm ? wpm : __int_as_float(0x7f800000);
+            }
+        }
+        // outputs: codeword, metric, winner, and u = x G^{(x)m} at the information positions
+        const bool fvalid = f < a.n_frames;
+        if (fvalid && a.cw_out && j < NW) a.cw_out[f * NW + j] = pick_word(cw, j);
+        if (fvalid && j == 0) {
+            if (a.pm_out) a.pm_out[f] = best_pm;
+            if (a.best_out) a.best_out[f] = best_d;
+        }
+        uint32_t u[NW];
+#pragma unroll
+        for (int w = 0; w < NW; w++) {
+            unsigned v = cw[w];
+            v ^= (v >> 1) & 0x55555555u;
+            v ^= (v >> 2) & 0x33333333u;
+            v ^= (v >> 4) & 0x0F0F0F0Fu;
+            v ^= (v >> 8) & 0x00FF00FFu;
+            if (M > 4) v ^= (v >> 16) & 0x0000FFFFu;
+            u[w] = v;
+        }
+#pragma unroll
+        for (int t = 5; t < M; t++) {
+            constexpr int one = 1;
+            const int dd = one << (t - 5);
+#pragma unroll
+            for (int w = 0; w < NW; w++)
+                if (!(w & dd)) u[w] ^= u[w | dd];
+        }
+        unsigned iw = 0;
+        for (int t = 0; t * FW < K; t++) {
+            const int q = j + FW * t;
+            unsigned b = 0;
+            if (q < K) {
+                const int pos = s_info[q];
+                b = (pick_word(u, pos >> 5) >> (pos & 31)) & 1u;
+            }
+            iw |= ((__ballot_sync(kFull, b) >> gbase) & gmask) << ((FW * t) & 31);
+        }
+        if (fvalid && j == 0) a.info_out[f] = iw;
+    }
+}
+
+}  // namespace rmdec_dev

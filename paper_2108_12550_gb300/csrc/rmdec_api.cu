@@ -152,6 +152,7 @@ struct rmdec_ctx {
     int m = 0, r = 0, P = 0, L = 1, n = 0, k = 0;
     rmdec_dtype dtype = RMDEC_LLR_F32;
     rmdec_hadamard hadamard = RMDEC_HADAMARD_SHUFFLE;
+    rmdec_kernel kernel = RMDEC_KERNEL_AUTO;
     std::vector<uint16_t> perms;  // host table in the documented layout
     std::vector<int> info;
     bool dirty = true;
@@ -213,6 +214,8 @@ bool lookup_kernel(rmdec_ctx* h, rmdec_host::KernelEntry* e) {
     if (h->algo == 1) return lookup_autssc(h->m, h->r, e);
     if (h->algo == 2) return lookup_mlroot(h->m, h->r, e);
     if (h->hadamard == RMDEC_HADAMARD_TENSOR) return lookup_pfht_tc(h->m, h->r, h->L, e);
+    if (h->kernel != RMDEC_KERNEL_WARP && lookup_pfht_ppt(h->m, h->r, h->L, h->P, e)) return true;
+    if (h->kernel == RMDEC_KERNEL_PATH) return false;
     if (h->L == 32) {
         if (h->m == 9) return lookup_pfht_l32_m9(h->r, e);
         if (h->m == 8) return lookup_pfht_l32_m8(h->r, e);
@@ -289,10 +292,15 @@ rmdec_status ensure_device(rmdec_ctx* h) {
     return RMDEC_OK;
 }
 
+// p-FHT-FSCL kernels whose CTA decodes one frame at a time with all its warps (the P
+// decoders split across them); the other kernels give each warp frames of its own.
+bool block_per_frame(const rmdec_ctx* h, const rmdec_host::KernelEntry& k) { return h->algo == 0 && !k.frames_per_warp; }
+
 // Widest CTA a handle's kernel accepts: pfht_kernel is built for up to kMaxWarps warps, and
 // more warps than decoders would idle.
-int max_warps_per_cta(const rmdec_ctx* h) {
-    if (h->algo == 2) return 8;  // one frame per warp
+int max_warps_per_cta(const rmdec_ctx* h, const rmdec_host::KernelEntry& k) {
+    if (h->algo == 2) return 8;           // one frame per warp
+    if (k.frames_per_warp) return 4;      // path-per-thread kernels: up to 128 threads
     return h->algo == 0 ? std::min(h->P, rmdec_dev::kMaxWarps) : 4;
 }
 
@@ -306,7 +314,7 @@ rmdec_status configure_shape(rmdec_ctx* h) {
     // launch in any order
     if ((e = cudaFuncSetAttribute(h->kern.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)) != cudaSuccess)
         return h->cuda_fail(e, "cudaFuncSetAttribute");
-    const int wmax = max_warps_per_cta(h);
+    const int wmax = max_warps_per_cta(h, h->kern);
     auto smem_for = [&](int W) { return (size_t)h->kern.fixed_bytes(h->P, h->k, W) + 16 + (size_t)W * h->kern.warp_bytes; };
     auto occ_for = [&](int W) {
         int o = 0;
@@ -334,8 +342,8 @@ rmdec_status configure_shape(rmdec_ctx* h) {
         // 5.73 M frames/s, 5 x 4 5.57 M, 10 x 2 5.45 M, 20 x 1 5.16 M)
         auto score = [&](int c) {
             const int occ = occ_for(c);
-            const bool even = h->algo != 0 || h->P % c == 0;
-            const bool two_each = h->algo != 0 || h->P >= 2 * c;
+            const bool even = !block_per_frame(h, h->kern) || h->P % c == 0;
+            const bool two_each = !block_per_frame(h, h->kern) || h->P >= 2 * c;
             return std::make_tuple(occ * c, even, two_each, occ >= 2, -c);
         };
         auto best = score(1);
@@ -373,7 +381,7 @@ rmdec_status launch(rmdec_ctx* h, const void* llr, int64_t n_frames, uint32_t* b
     int W = h->warps, per_sm = h->blocks_per_sm;
     size_t smem = h->smem;
     const int64_t cap0 = (int64_t)h->sm_count * h->blocks_per_sm;
-    if (h->auto_shape && !h->req_ctas && h->algo == 0 && n_frames <= 4 * cap0) {
+    if (h->auto_shape && !h->req_ctas && block_per_frame(h, h->kern) && n_frames <= 4 * cap0) {
         auto cost = [&](int c) {
             const int64_t cap = (int64_t)h->sm_count * h->occ_w[c];
             return ((n_frames + cap - 1) / cap) * (int64_t)((h->P + c - 1) / c);
@@ -406,8 +414,9 @@ rmdec_status launch(rmdec_ctx* h, const void* llr, int64_t n_frames, uint32_t* b
     a.single_start = h->single_start ? 1 : 0;
     const int64_t cap = (int64_t)h->sm_count * per_sm;
     // p-FHT-FSCL and Aut-SSC CTAs take one frame at a time; the first-order/parity-check root
-    // kernel decodes one frame per warp
-    const int64_t want = h->algo == 2 ? (n_frames + W - 1) / W : n_frames;
+    // kernel decodes one frame per warp, the path-per-thread kernel frames_per_warp per warp
+    const int64_t fpw = h->algo == 2 ? 1 : h->kern.frames_per_warp;
+    const int64_t want = fpw ? (n_frames + W * fpw - 1) / (W * fpw) : n_frames;
     const unsigned grid = (unsigned)std::min<int64_t>(want, cap);
     void* args[] = {&a};
     nvtxRangePushA(h->algo == 1 ? "rmdec_decode aut-ssc" : "rmdec_decode pfht");
@@ -503,6 +512,7 @@ rmdec_status member_info(rmdec_ctx* h, bool prepare, MemberInfo* out) {
     out->nrec = h->dirty ? 0 : h->kern.nrec;
     out->device = h->dirty ? -1 : h->device;
     out->wave = (h->dirty || h->shape_dirty) ? 0 : (int64_t)h->sm_count * h->blocks_per_sm;
+    out->path_kernel = !h->dirty && h->kern.frames_per_warp != 0;
     return RMDEC_OK;
 }
 }  // namespace rmdec_host
@@ -566,6 +576,22 @@ rmdec_status rmdec_set_hadamard(rmdec_t h, rmdec_hadamard mode) {
         return h->fail(RMDEC_EINVAL, "no tensor-core Hadamard kernel for this decoder (RM(2|3, 9), L in {4, 8})");
     if (mode != h->hadamard) {
         h->hadamard = mode;
+        h->dirty = true;  // the next decode looks up the kernel again
+        h->shape_dirty = true;
+    }
+    return RMDEC_OK;
+}
+
+rmdec_status rmdec_set_kernel(rmdec_t h, rmdec_kernel kernel) {
+    if (!h) return RMDEC_EINVAL;
+    if (kernel != RMDEC_KERNEL_AUTO && kernel != RMDEC_KERNEL_WARP && kernel != RMDEC_KERNEL_PATH)
+        return h->fail(RMDEC_EINVAL, "unknown kernel choice %d", (int)kernel);
+    rmdec_host::KernelEntry e;
+    if (kernel == RMDEC_KERNEL_PATH &&
+        (h->algo != 0 || h->hadamard != RMDEC_HADAMARD_SHUFFLE || !rmdec_host::lookup_pfht_ppt(h->m, h->r, h->L, h->P, &e)))
+        return h->fail(RMDEC_EINVAL, "no path-per-thread kernel for this decoder (RM(2, m), 4 <= m <= 7, L <= 8)");
+    if (kernel != h->kernel) {
+        h->kernel = kernel;
         h->dirty = true;  // the next decode looks up the kernel again
         h->shape_dirty = true;
     }
@@ -748,8 +774,8 @@ rmdec_status rmdec_autotune(rmdec_t h, int64_t n_frames, const char* cache_path,
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, h->device);
     char key[512];
-    snprintf(key, sizeof key, "%.200s|algo%d|m%d|r%d|P%d|L%d|dt%d", prop.name, h->algo, h->m, h->r, h->P, h->L,
-             (int)h->dtype);
+    snprintf(key, sizeof key, "%.200s|algo%d|m%d|r%d|P%d|L%d|dt%d|ppt%d", prop.name, h->algo, h->m, h->r, h->P, h->L,
+             (int)h->dtype, h->kern.frames_per_warp ? 1 : 0);
     for (char* c = key; *c; c++)
         if (*c == ' ') *c = '_';
     if (cache_path) {
@@ -804,7 +830,7 @@ rmdec_status rmdec_autotune(rmdec_t h, int64_t n_frames, const char* cache_path,
     cudaEventCreate(&e1);
     float best_ms = 1e30f;
     int best_w = 0;
-    const int wmax = max_warps_per_cta(h);
+    const int wmax = max_warps_per_cta(h, h->kern);
     for (int w = 1; w <= wmax; w++) {
         h->req_warps = w;
         h->req_ctas = 0;
@@ -997,7 +1023,7 @@ extern "C" rmdec_status rmdec_decode_noalloc(rmdec_t h, const void* llr_dev, int
     if ((e = cudaFuncSetAttribute(kern.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)) != cudaSuccess)
         return h->cuda_fail(e, "cudaFuncSetAttribute");
     // launch shape: the handle's requested one, else the default rule of rmdec_set_tuning
-    const int wmax = max_warps_per_cta(h);
+    const int wmax = max_warps_per_cta(h, kern);
     auto smem_for = [&](int W) { return (size_t)kern.fixed_bytes(h->P, h->k, W) + 16 + (size_t)W * kern.warp_bytes; };
     auto occ_for = [&](int W) {
         int o = 0;
@@ -1009,8 +1035,8 @@ extern "C" rmdec_status rmdec_decode_noalloc(rmdec_t h, const void* llr_dev, int
     if (!W) {
         auto score = [&](int c) {
             const int occ = occ_for(c);
-            const bool even = h->algo != 0 || h->P % c == 0;
-            const bool two_each = h->algo != 0 || h->P >= 2 * c;
+            const bool even = !block_per_frame(h, kern) || h->P % c == 0;
+            const bool two_each = !block_per_frame(h, kern) || h->P >= 2 * c;
             return std::make_tuple(occ * c, even, two_each, occ >= 2, -c);
         };
         auto best = score(1);

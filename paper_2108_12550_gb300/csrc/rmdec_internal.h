@@ -25,6 +25,7 @@ struct KernelEntry {
     int warp_bytes = 0;        // shared memory per warp
     int nrec = 0;              // permutation maps per decoder held in block shared memory
     int (*fixed_bytes)(int P, int K, int W) = nullptr;
+    int frames_per_warp = 0;   // path-per-thread kernels: frames a warp decodes at once (else 0)
 };
 
 // p-FHT-FSCL kernels: one lookup per code length m (instantiated in inst_m<m>.cu).
@@ -42,6 +43,10 @@ bool lookup_pfht_r4_m9(int L, KernelEntry* e);
 bool lookup_pfht_l32_small(int m, int r, KernelEntry* e);  // m = 4 .. 7
 bool lookup_pfht_l32_m8(int r, KernelEntry* e);
 bool lookup_pfht_l32_m9(int r, KernelEntry* e);
+
+// Path-per-thread kernels for RM(2, m), 4 <= m <= 7, L in {1, 2, 4, 8} (inst_ppt.cu); the
+// entry's shared-memory sizes depend on the decoder count P.
+bool lookup_pfht_ppt(int m, int r, int L, int P, KernelEntry* e);
 
 // p-FHT-FSCL kernels whose FHTL nodes use the tensor cores (inst_tc.cu).
 bool lookup_pfht_tc(int m, int r, int L, KernelEntry* e);
@@ -65,6 +70,7 @@ struct MemberInfo {
     int nrec = 0;  // permutation maps per decoder held in block shared memory
     int device = -1;
     int64_t wave = 0;  // CTAs of the handle's own launch resident at once (valid after prepare)
+    bool path_kernel = false;  // decodes with the path-per-thread kernel (valid after prepare)
 };
 // Fills *out from the handle; with prepare = true first uploads the handle's tables to the
 // current device and fixes its own launch shape (errors are recorded on the handle, see

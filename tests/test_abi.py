@@ -133,3 +133,17 @@ def test_tensor_core_hadamard_availability_is_checked_on_the_host():
     with pytest.raises(pkg.RmdecError):
         pkg.Group([a])  # grouped launches have no tensor-core variant
 
+
+
+def test_kernel_choice_is_checked_on_the_host():
+    d = pkg.Decoder(7, 2, 8, 4)
+    d.set_kernel("path")
+    d.set_kernel("warp")
+    d.set_kernel("auto")
+    for bad in [pkg.Decoder(9, 2, 4, 4), pkg.Decoder(6, 3, 4, 4), pkg.Decoder(6, 2, 4, 16),
+                pkg.Decoder(7, 2, 8, algo="autssc"), pkg.Decoder(7, 1, 2, 4)]:
+        with pytest.raises(pkg.RmdecError) as ei:
+            bad.set_kernel("path")
+        assert ei.value.status == pkg.EINVAL
+    assert d._lib.rmdec_set_kernel(d._h, 7) == pkg.EINVAL
+    pkg.Decoder(4, 2, 128, 8).set_kernel("path")

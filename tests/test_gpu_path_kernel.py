@@ -1,0 +1,123 @@
+"""The path-per-thread kernel (one thread per list path, RM(2, m) with 4 <= m <= 7, L <= 8)
+against the warp-per-decoder kernel and the oracle, through the C ABI.
+
+Both kernels run the same method (Algorithms 2-5), so on integer LLRs (INT8, INT16, FP32
+holding integers) every output is identical: information bits, codewords, metrics, winning
+decoder. On real-valued FP32 and FP16 LLRs they may differ only where two FHTL candidates of
+one path round to the same FP32 metric; the bound below is far above the measured rate, and
+every returned metric must be the discrepancy of the returned word."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle as O  # noqa: E402
+import paper_2108_12550_gb300 as pkg  # noqa: E402
+from paper_2108_12550_gb300 import inputs as I  # noqa: E402
+
+
+def _run(dec, x):
+    bits, cw, pm, best = dec.decode_debug(torch.from_numpy(np.ascontiguousarray(x)).cuda())
+    torch.cuda.synchronize()
+    return (bits.cpu().numpy(), cw.cpu().numpy(), pm.cpu().numpy(), best.cpu().numpy())
+
+
+def _both(m, r, P, L, x, dtype, perms):
+    out = {}
+    for k in ("warp", "path"):
+        dec = pkg.Decoder(m, r, P, L, dtype=dtype, perms=perms)
+        dec.set_kernel(k)
+        out[k] = _run(dec, x)
+    return out["warp"], out["path"]
+
+
+# (m, P, L, frames): every list size, batches of decoders (P * L > 32), idle decoder slots
+# (P * L not a power of two) and ragged frame counts (not a multiple of the frames per warp)
+CASES = [(m, P, L, nf) for m in (4, 5, 6, 7) for (P, L, nf) in
+         [(1, 1, 333), (3, 2, 250), (8, 4, 200), (20, 4, 61), (2, 8, 97), (5, 8, 33)]]
+
+
+@pytest.mark.parametrize("m,P,L,nf", CASES, ids=lambda v: str(v))
+def test_integer_llrs_identical_to_the_warp_kernel(m, P, L, nf):
+    r = 2
+    fr = I.make_frames(m, r, nf, 1.5 + 0.25 * L, seed=500 + 10 * m + L)
+    q = I.quantize_i8(fr["llr"])
+    perms = I.perm_table(m, r, P, L, seed=m + 3 * L + P)
+    w, p = _both(m, r, P, L, q, "i8", perms)
+    for a, b, name in zip(w, p, ("bits", "cw", "pm", "best")):
+        assert np.array_equal(a, b), name
+
+
+@pytest.mark.parametrize("m,P,L", [(5, 4, 2), (7, 8, 4), (6, 3, 8), (4, 2, 1)])
+def test_integer_llrs_match_the_oracle(m, P, L):
+    r = 2
+    fr = I.make_frames(m, r, 300, 2.0, seed=70 + m)
+    q = I.quantize_i8(fr["llr"])
+    perms = I.perm_table(m, r, P, L, seed=9 * m + L)
+    ref = O.decode(m, r, P, L, perms, q.astype(np.int64), integer=True)
+    dec = pkg.Decoder(m, r, P, L, dtype="i8", perms=perms)
+    dec.set_kernel("path")
+    bits, cw, pm, best = _run(dec, q)
+    assert np.array_equal(pkg.unpack_bits(cw, dec.n), ref["cw"])
+    assert np.array_equal(pm.astype(np.int64), ref["pm"]) and np.array_equal(best, ref["best"])
+    assert np.array_equal(pkg.unpack_bits(bits, dec.k), ref["info"])
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "i16"])
+@pytest.mark.parametrize("m,P,L", [(5, 4, 2), (7, 8, 4), (6, 20, 8)])
+def test_other_input_types_agree_with_the_warp_kernel(m, P, L, dtype):
+    r = 2
+    fr = I.make_frames(m, r, 1500, 2.5, seed=90 + m + L)
+    if dtype == "f32":
+        x = fr["llr"].astype(np.float32)
+    elif dtype == "f16":
+        x = fr["llr"].astype(np.float16)
+    else:
+        x = np.clip(np.rint(fr["llr"] * 256), -32767, 32767).astype(np.int16)
+    perms = I.perm_table(m, r, P, L, seed=5 * m + L)
+    w, p = _both(m, r, P, L, x, dtype, perms)
+    if dtype == "i16":
+        for a, b in zip(w, p):
+            assert np.array_equal(a, b)
+        return
+    same = np.all(w[1] == p[1], axis=1)
+    assert same.mean() >= 0.998, same.mean()
+    # every returned metric is the discrepancy of the returned word
+    xf = x.astype(np.float64)
+    cw = pkg.unpack_bits(p[1], 1 << m)
+    disc = np.sum(np.abs(xf) * (cw != (xf < 0)), axis=1)
+    np.testing.assert_allclose(p[2], disc, rtol=1e-4, atol=1e-4 * np.abs(xf).mean())
+
+
+def test_tuning_shapes_and_tiny_batches():
+    m, r, P, L = 7, 2, 8, 4
+    fr = I.make_frames(m, r, 700, 2.0, seed=12)
+    q = I.quantize_i8(fr["llr"])
+    dec = pkg.Decoder(m, r, P, L, dtype="i8", perm_seed=4)
+    ref = _run(dec, q)
+    for w in (1, 2, 3, 4):
+        dec.set_tuning(w, 0)
+        assert all(np.array_equal(a, b) for a, b in zip(ref, _run(dec, q))), w
+    dec.set_tuning(0, 1)
+    assert all(np.array_equal(a, b) for a, b in zip(ref, _run(dec, q)))
+    dec.set_tuning(0, 0)
+    for n in (1, 2, 5):  # fewer frames than a warp decodes at once
+        got = _run(dec, q[:n])
+        assert all(np.array_equal(a[:n], b) for a, b in zip(ref, got)), n
+    small = pkg.Decoder(5, 2, 1, 1, dtype="i8", perm_seed=2)  # 32 frames per warp
+    fr5 = I.make_frames(5, 2, 77, 2.0, seed=3)
+    q5 = I.quantize_i8(fr5["llr"])
+    a = _run(small, q5)
+    small.set_kernel("warp")
+    assert all(np.array_equal(x, y) for x, y in zip(a, _run(small, q5)))
+
+
+def test_kernel_choice_is_validated():
+    with pytest.raises(pkg.RmdecError):
+        pkg.Decoder(9, 2, 4, 4).set_kernel("path")  # no path-per-thread kernel for m = 9
+    with pytest.raises(pkg.RmdecError):
+        pkg.Decoder(6, 3, 4, 4).set_kernel("path")  # nor for r = 3
+    with pytest.raises(pkg.RmdecError):
+        pkg.Decoder(6, 2, 4, 16).set_kernel("path")  # nor for L = 16
+    pkg.Decoder(7, 2, 20, 8).set_kernel("path")
