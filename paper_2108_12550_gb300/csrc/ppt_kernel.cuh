@@ -67,6 +67,11 @@ struct Ppt {
     static constexpr int H = N / 2;
     static constexpr int NW = (N + 31) / 32;
     static constexpr int NREC = 2 * L;  // root candidates per decoder (one permuted level)
+    // The LLRs of level m-1 wait in shared memory (a column per lane) while the leaf RM(1, m-2)
+    // is decoded, instead of in registers: the register peak, and so the resident warps, then
+    // follow the largest leaf alone.
+    static constexpr bool PEND_SMEM = M >= 6;
+    static constexpr int PEND_FLOATS = PEND_SMEM ? H * 32 : 0;  // per warp
     static_assert(M >= 4 && M <= 7, "short codes");
     static_assert(L == 1 || L == 2 || L == 4 || L == 8, "list size");
 
@@ -74,6 +79,7 @@ struct Ppt {
         const float* y;         // the frame's LLRs (shared memory)
         const uint16_t* rec;    // the decoder's 2L composed root records (shared memory)
         uint8_t* sel;           // the warp's 32-byte selection scratch
+        float* pend;            // the warp's level-(m-1) LLRs: value i of lane t at [32 i + t]
         int dbase;              // lane of the decoder's path 0
         int l;                  // this lane's path
         bool single;            // paths 1..L-1 start inactive (metric +inf)
@@ -125,7 +131,7 @@ struct Ppt {
     // candidates (k, sign of c_k) with PM' = PM + (sum|alpha| - |c_k|) / 2; the L best over the
     // decoder's paths by (PM', path, k) survive. pend: the PC pending LLRs a new path copies.
     template <int S, int OFF, int PC, int PA>
-    __device__ __forceinline__ static void fht_leaf(const Ctx& c, Path& p, float (&v)[1 << S], float (&pend)[PA]) {
+    __device__ __forceinline__ static int fht_leaf(const Ctx& c, Path& p, float (&v)[1 << S], float (&pend)[PA]) {
         constexpr int NS = 1 << S;
         constexpr int T = cmin(L, NS);
         static_assert(T == L, "every path offers L candidates");
@@ -267,6 +273,7 @@ struct Ppt {
         } else {
             put_bits<OFF, NS>(p, pattern(k, 0));
         }
+        return par;  // the parent path (this lane's new path descends from it)
     }
 
     // --------------------------------------------------------------- SPCL leaf ---
@@ -378,11 +385,27 @@ struct Ppt {
         } else {
             constexpr int HS = 1 << (S - 1);
             float ch[HS];
+            if constexpr (PEND_SMEM && S == M - 1) {
+                // park the node's LLRs in this lane's column; the new path reads its parent's
+                const int lane = c.dbase + c.l;
+                __syncwarp();  // every lane has read the previous decoder's columns
 #pragma unroll
-            for (int i = 0; i < HS; i++) ch[i] = fminsum(a[i], a[i + HS]);
-            fht_leaf<S - 1, OFF, 1 << S>(c, p, ch, a);
+                for (int i = 0; i < (1 << S); i++) c.pend[32 * i + lane] = a[i];
+                __syncwarp();
 #pragma unroll
-            for (int i = 0; i < HS; i++) ch[i] = g_fn(a[i], a[i + HS], bit(p, OFF + i));
+                for (int i = 0; i < HS; i++) ch[i] = fminsum(a[i], a[i + HS]);
+                float none[1];
+                const int par = fht_leaf<S - 1, OFF, 0>(c, p, ch, none);
+                const float* pa = c.pend + c.dbase + par;
+#pragma unroll
+                for (int i = 0; i < HS; i++) ch[i] = g_fn(pa[32 * i], pa[32 * (i + HS)], bit(p, OFF + i));
+            } else {
+#pragma unroll
+                for (int i = 0; i < HS; i++) ch[i] = fminsum(a[i], a[i + HS]);
+                fht_leaf<S - 1, OFF, 1 << S>(c, p, ch, a);
+#pragma unroll
+                for (int i = 0; i < HS; i++) ch[i] = g_fn(a[i], a[i + HS], bit(p, OFF + i));
+            }
             node2<S - 1, OFF + HS>(c, p, ch);
             combine<OFF, HS>(p);
         }
@@ -493,8 +516,13 @@ struct Ppt {
 };
 
 // Decodes the frames of the job, one warp per 32 / FW frames (see Ppt).
+// Resident CTAs of 4 warps the register budget is sized for: 168 registers per thread for
+// m >= 6 (measured on RM(2,7) P=8 L=4: 79.0 M frames/s, against 71.0 M at 128 registers, where
+// the largest leaf spills), 102 for shorter codes.
+__host__ __device__ constexpr int ppt_min_blocks(int m) { return m >= 6 ? 3 : 5; }
+
 template <int M, int L>
-__global__ void __launch_bounds__(128, (M >= 6 ? 3 : 4)) ppt_kernel(LaunchArgs a) {
+__global__ void __launch_bounds__(128, ppt_min_blocks(M)) ppt_kernel(LaunchArgs a) {
     using D = Ppt<M, L>;
     constexpr int N = D::N, NW = D::NW, NREC = D::NREC;
     constexpr int K = 1 + M + M * (M - 1) / 2;  // information bits of RM(2, m)
@@ -509,19 +537,21 @@ __global__ void __launch_bounds__(128, (M >= 6 ? 3 : 4)) ppt_kernel(LaunchArgs a
     uint16_t* s_rec = reinterpret_cast<uint16_t*>(smem);
     uint16_t* s_info = s_rec + rec_elems;
     const int tables = ((rec_elems * 2 + K * 2) + 15) / 16 * 16;
-    const int warp_bytes = FPW * N * 4 + 32;
+    const int warp_bytes = (D::PEND_FLOATS + FPW * N) * 4 + 32;
     for (int i = threadIdx.x; i < rec_elems; i += blockDim.x) s_rec[i] = a.recs[i];
     for (int i = threadIdx.x; i < K; i += blockDim.x) s_info[i] = a.info[i];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float* s_y = reinterpret_cast<float*>(smem + tables + warp * warp_bytes);
-    uint8_t* s_sel = smem + tables + warp * warp_bytes + FPW * N * 4;
+    float* s_pend = reinterpret_cast<float*>(smem + tables + warp * warp_bytes);
+    float* s_y = s_pend + D::PEND_FLOATS;
+    uint8_t* s_sel = smem + tables + warp * warp_bytes + (D::PEND_FLOATS + FPW * N) * 4;
     const int grp = lane / FW, j = lane % FW, gbase = grp * FW;
     const int DPB = FW / L;  // decoders per batch
     const int ds = j / L;
     typename D::Ctx c;
     c.y = s_y + grp * N;
     c.sel = s_sel;
+    c.pend = s_pend;
     c.dbase = gbase + ds * L;
     c.l = j % L;
     c.single = a.single_start != 0;
