@@ -196,7 +196,9 @@ rmdec_status rmdec_poll(rmdec_t h, uint64_t ticket, int64_t timeout_us);
 /* Launch shape: warps per CTA (1..20, at most P; Aut-SSC handles use at most 4; the decoders
  * of a frame are split across a CTA's warps; path-per-thread kernels (rmdec_set_kernel) take
  * 1..4 warps, each decoding its own frames) and a cap on resident CTAs per SM (0 = the
- * occupancy limit); 0 warps = the default: the most resident warps per SM, then warps that
+ * occupancy limit); 0 warps = the default: for p-FHT-FSCL kernels whose CTA decodes one frame,
+ * 4 (else 3, else 2) warps when that splits the P decoders evenly and keeps at least two thirds
+ * of the most resident warps per SM; otherwise the most resident warps per SM, then warps that
  * split the P decoders evenly, then two or more decoders per warp and two or more CTAs per
  * SM, then the narrowest CTA; a launch of at most four waves of that shape takes the shape
  * with the fewest waves x rounds of decoders per warp instead (wider CTAs run more of each

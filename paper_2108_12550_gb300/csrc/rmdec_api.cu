@@ -304,6 +304,44 @@ int max_warps_per_cta(const rmdec_ctx* h, const rmdec_host::KernelEntry& k) {
     return h->algo == 0 ? std::min(h->P, rmdec_dev::kMaxWarps) : 4;
 }
 
+// Default warps per CTA, given the resident CTAs occ_for(W) of each width W <= wmax.
+// Kernels whose CTA decodes one frame with all its warps: four warps (else three, else two)
+// when that width splits the P decoders evenly and keeps at least two thirds of the most
+// resident warps. Its warps run their decoders in lockstep (a block barrier at every leaf),
+// which keeps them on the same code; the trees of the longer codes exceed the instruction
+// caches, so this pays more than the last resident warps. Measured (M frames/s, FP32, L = 4;
+// the narrowest-CTA default that preceded it in parentheses): RM(2,9) P=20 6.46 at 4 x 5 (the
+// same shape), RM(3,9) P=20 2.90 (2.73 at 2 x 10), RM(3,9) P=8 7.11 (6.65), RM(3,8) P=8 12.86
+// (12.15 at 1 x 20), RM(2,10) P=8 5.93 (5.35 at 2 x 5), RM(3,10) P=8 2.79 (2.28 at 6 x 2); no
+// other width was more than 6% faster on any of 15 codes and list sizes.
+// Otherwise, and for the kernels whose warps decode frames of their own: the most resident
+// warps per SM; among equals, widths that split the P decoders evenly, then at least two
+// decoders per warp and two or more CTAs per SM (a lone decoder per warp, or a lone CTA,
+// leaves the SM idle at every frame boundary), then the narrowest CTA.
+template <typename Occ>
+int default_warps(const rmdec_ctx* h, const rmdec_host::KernelEntry& k, int wmax, Occ occ_for) {
+    const bool bpf = block_per_frame(h, k);
+    int most = 0;
+    for (int c = 1; c <= wmax; c++) most = std::max(most, occ_for(c) * c);
+    if (bpf)
+        for (int c : {4, 3, 2})
+            if (c <= wmax && h->P % c == 0 && 3 * occ_for(c) * c >= 2 * most) return c;
+    auto score = [&](int c) {
+        const int occ = occ_for(c);
+        const bool even = !bpf || h->P % c == 0;
+        const bool two_each = !bpf || h->P >= 2 * c;
+        return std::make_tuple(occ * c, even, two_each, occ >= 2, -c);
+    };
+    auto best = score(1);
+    int W = 1;
+    for (int c = 2; c <= wmax; c++)
+        if (score(c) > best) {
+            best = score(c);
+            W = c;
+        }
+    return W;
+}
+
 // Launch shape: warps per CTA (decoders of a frame split across warps) and resident CTAs.
 rmdec_status configure_shape(rmdec_ctx* h) {
     if (!h->shape_dirty) return RMDEC_OK;
@@ -332,28 +370,7 @@ rmdec_status configure_shape(rmdec_ctx* h) {
     if (!W)
         if (const char* s = getenv("RMDEC_WARPS")) W = atoi(s);
     h->auto_shape = W == 0;
-    if (!W) {
-        // default: the most resident warps per SM; among equals, warps that split the P
-        // decoders evenly (which also lets the kernel align its warps at every leaf), then at
-        // least two decoders per warp and at least two CTAs per SM (a lone decoder per warp,
-        // or a lone CTA, leaves the SM idle at every frame boundary), then the narrowest CTA:
-        // more CTAs per SM hide each other's barrier waits, while the leaf barriers keep the
-        // warps of one CTA on the same code (measured on RM(2,9) P=20 L=4: 4 warps x 5 CTAs
-        // 5.73 M frames/s, 5 x 4 5.57 M, 10 x 2 5.45 M, 20 x 1 5.16 M)
-        auto score = [&](int c) {
-            const int occ = occ_for(c);
-            const bool even = !block_per_frame(h, h->kern) || h->P % c == 0;
-            const bool two_each = !block_per_frame(h, h->kern) || h->P >= 2 * c;
-            return std::make_tuple(occ * c, even, two_each, occ >= 2, -c);
-        };
-        auto best = score(1);
-        W = 1;
-        for (int c = 2; c <= wmax; c++)
-            if (score(c) > best) {
-                best = score(c);
-                W = c;
-            }
-    }
+    if (!W) W = default_warps(h, h->kern, wmax, occ_for);
     W = std::max(1, std::min(wmax, W));
     h->warps = W;
     h->smem = smem_for(W);
@@ -1032,21 +1049,7 @@ extern "C" rmdec_status rmdec_decode_noalloc(rmdec_t h, const void* llr_dev, int
         return o;
     };
     int W = std::max(0, std::min(wmax, h->req_warps));
-    if (!W) {
-        auto score = [&](int c) {
-            const int occ = occ_for(c);
-            const bool even = !block_per_frame(h, kern) || h->P % c == 0;
-            const bool two_each = !block_per_frame(h, kern) || h->P >= 2 * c;
-            return std::make_tuple(occ * c, even, two_each, occ >= 2, -c);
-        };
-        auto best = score(1);
-        W = 1;
-        for (int c = 2; c <= wmax; c++)
-            if (score(c) > best) {
-                best = score(c);
-                W = c;
-            }
-    }
+    if (!W) W = default_warps(h, kern, wmax, occ_for);
     const int occ = occ_for(W);
     if (occ < 1) return h->fail(RMDEC_EINVAL, "kernel cannot be resident with %d warps per CTA", W);
     const int per_sm = h->req_ctas ? std::min(h->req_ctas, occ) : occ;

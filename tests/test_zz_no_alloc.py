@@ -68,3 +68,24 @@ def test_noalloc_decode_equals_decode_on_consecutive_calls():
     assert np.mean(np.any(ua != fa["u"], axis=1)) < 0.01
     a.close()
     b.close()
+
+
+@pytest.mark.gpu
+def test_noalloc_decode_with_the_path_per_thread_kernel():
+    # short codes decode with the path-per-thread kernel; its launch (several frames per warp)
+    # reads the same fixed tables
+    torch = pytest.importorskip("torch")
+    lib = pkg.load_library()
+    stream = torch.cuda.current_stream().cuda_stream
+    for (m, P, L, dt, nf) in [(7, 8, 4, "i8", 501), (5, 4, 2, "f32", 333)]:
+        d = pkg.Decoder(m, 2, P, L, perm_seed=21, dtype=dt)
+        fr = I.make_frames(m, 2, nf, 2.5, seed=40 + m)
+        x = fr["llr"].astype(np.float32) if dt == "f32" else I.quantize_i8(fr["llr"])
+        xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        ref = d.decode(xd)
+        torch.cuda.synchronize()
+        out = torch.full_like(ref, -1)
+        assert _call(lib, d, xd, out, stream) == pkg.OK, lib.rmdec_last_error(d._h)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref), (m, P, L)
+        d.close()
