@@ -33,6 +33,7 @@ WORKLOADS = {
     "rm27_p8_l4": (7, 2, 8, 4, 3.0, 1 << 20),
     "rm25_p4_l2": (5, 2, 4, 2, 3.0, 1 << 21),
     "rm39_p16_l8": (9, 3, 16, 8, 4.0, 1 << 16),
+    "rm39_p20_l4": (9, 3, 20, 4, 3.0, 1 << 17),  # the serving mix's costliest code
 }
 METRIC = "frames/s RM(2,9) P=20 L=4 at FER~1e-4 Eb/N0; p50/p99 latency, mixed load"
 # DRAM bytes per frame of one ncu capture of pfht_kernel<9,2,4> (16,384 frames: 33,641,728 B
