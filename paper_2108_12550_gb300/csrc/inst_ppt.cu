@@ -11,7 +11,7 @@ bool ppt_entry(int P, KernelEntry* e) {
     const int fw = rmdec_dev::ppt_frame_lanes(M, L, P);
     e->fn = reinterpret_cast<const void*>(&rmdec_dev::ppt_kernel<M, L>);
     e->frames_per_warp = 32 / fw;
-    e->warp_bytes = (D::PEND_FLOATS + e->frames_per_warp * D::N) * 4 + 32;
+    e->warp_bytes = (D::PEND_FLOATS + e->frames_per_warp * rmdec_dev::ppt_frame_stride(M, e->frames_per_warp)) * 4 + 32;
     e->nrec = 0;  // the maps sit in the fixed part
     e->fixed_bytes = [](int P2, int K, int) {
         return ((P2 * 2 * rmdec_dev::Ppt<M, L>::NREC * rmdec_dev::kRec * 2 + K * 2) + 15) / 16 * 16;

@@ -31,7 +31,7 @@
 namespace rmdec_dev {
 
 // Lanes per frame group: the decoders of one batch (L lanes each); at least N / 32 lanes, so
-// that a warp stages at most 32 N / FW <= 1024 LLRs (4 KB).
+// that a warp stages at most 32 N / FW <= 1024 LLRs (4 KB, plus the padding of ppt_frame_stride).
 __host__ __device__ constexpr int ppt_pow2_ceil(int x) { return x <= 1 ? 1 : 2 * ppt_pow2_ceil((x + 1) / 2); }
 __host__ __device__ inline int ppt_frame_lanes(int m, int L, int P) {
     const int n32 = m >= 5 ? (1 << m) / 32 : 1;
@@ -42,6 +42,15 @@ __host__ __device__ inline int ppt_frame_lanes(int m, int L, int P) {
 }
 
 // trailing zeros of 0 < n < 128 (folds to a constant for constant n, unlike a recursion)
+// Floats between the starts of consecutive staged frames of a warp: N, padded when several
+// frames share the warp so that their starts fall on distinct banks, 32 / FPW banks apart (at
+// least 4, which keeps every frame 16-byte aligned for the vector loads).
+__host__ __device__ inline int ppt_frame_stride(int m, int fpw) {
+    const int n = 1 << m;
+    if (fpw <= 1) return n;
+    const int spacing = 32 / fpw > 4 ? 32 / fpw : 4;
+    return n + (((spacing - n) % 32) + 32) % 32;
+}
 __host__ __device__ constexpr int ctz7(int n) {
     return (n & 1) ? 0 : (n & 2) ? 1 : (n & 4) ? 2 : (n & 8) ? 3 : (n & 16) ? 4 : (n & 32) ? 5 : 6;
 }
@@ -530,6 +539,7 @@ __global__ void __launch_bounds__(128, ppt_min_blocks(M)) ppt_kernel(LaunchArgs 
     extern __shared__ __align__(16) uint8_t smem[];
     const int FW = ppt_frame_lanes(M, L, a.P);
     const int FPW = 32 / FW;
+    const int YS = ppt_frame_stride(M, FPW);  // floats per staged frame
     const int W = blockDim.x >> 5;
     // shared memory: the P decoders' maps and inverse maps as in the device table, the
     // information positions, then per warp its frames' LLRs and a selection scratch
@@ -537,19 +547,19 @@ __global__ void __launch_bounds__(128, ppt_min_blocks(M)) ppt_kernel(LaunchArgs 
     uint16_t* s_rec = reinterpret_cast<uint16_t*>(smem);
     uint16_t* s_info = s_rec + rec_elems;
     const int tables = ((rec_elems * 2 + K * 2) + 15) / 16 * 16;
-    const int warp_bytes = (D::PEND_FLOATS + FPW * N) * 4 + 32;
+    const int warp_bytes = (D::PEND_FLOATS + FPW * YS) * 4 + 32;
     for (int i = threadIdx.x; i < rec_elems; i += blockDim.x) s_rec[i] = a.recs[i];
     for (int i = threadIdx.x; i < K; i += blockDim.x) s_info[i] = a.info[i];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* s_pend = reinterpret_cast<float*>(smem + tables + warp * warp_bytes);
     float* s_y = s_pend + D::PEND_FLOATS;
-    uint8_t* s_sel = smem + tables + warp * warp_bytes + (D::PEND_FLOATS + FPW * N) * 4;
+    uint8_t* s_sel = smem + tables + warp * warp_bytes + (D::PEND_FLOATS + FPW * YS) * 4;
     const int grp = lane / FW, j = lane % FW, gbase = grp * FW;
     const int DPB = FW / L;  // decoders per batch
     const int ds = j / L;
     typename D::Ctx c;
-    c.y = s_y + grp * N;
+    c.y = s_y + grp * YS;
     c.sel = s_sel;
     c.pend = s_pend;
     c.dbase = gbase + ds * L;
@@ -570,7 +580,8 @@ __global__ void __launch_bounds__(128, ppt_min_blocks(M)) ppt_kernel(LaunchArgs 
                 if (f0 + (int64_t)(i * per) / N >= a.n_frames) continue;
                 const uint4 q = src[i];
                 const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
-                float4* dst = reinterpret_cast<float4*>(s_y + i * per);
+                const int q0 = i * per;  // first value of the chunk; chunks never straddle frames
+                float4* dst = reinterpret_cast<float4*>(s_y + (q0 / N) * YS + q0 % N);
                 if (a.dtype == IN_F32) {
                     dst[0] = make_float4(__uint_as_float(wv[0]), __uint_as_float(wv[1]), __uint_as_float(wv[2]),
                                          __uint_as_float(wv[3]));
