@@ -34,6 +34,7 @@ WORKLOADS = {
     "rm25_p4_l2": (5, 2, 4, 2, 3.0, 1 << 21),
     "rm39_p16_l8": (9, 3, 16, 8, 4.0, 1 << 16),
     "rm39_p20_l4": (9, 3, 20, 4, 3.0, 1 << 17),  # the serving mix's costliest code
+    "rm28_p8_l4": (8, 2, 8, 4, 3.0, 1 << 19),  # a serving-mix code
 }
 METRIC = "frames/s RM(2,9) P=20 L=4 at FER~1e-4 Eb/N0; p50/p99 latency, mixed load"
 # DRAM bytes per frame of one ncu capture of pfht_kernel<9,2,4> (16,384 frames: 33,641,728 B
@@ -504,7 +505,7 @@ def main():
     ap.add_argument("--frames", type=int, default=0, help="frames per step (default per workload)")
     ap.add_argument("--dtype", default="f32", choices=["f32", "i8", "f16", "i16"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "warp", "path"],
-                    help="decoder kernel: warp per decoder, thread per path (RM(2, m <= 7)), or auto")
+                    help="decoder kernel: warp per decoder, thread per path (RM(2, m <= 8)), or auto")
     ap.add_argument("--hadamard", default="shuffle", choices=["shuffle", "tensor"],
                     help="FHT of the FHTL nodes: FP32 butterflies or FP16 tensor-core products")
     ap.add_argument("--cpu-frames", type=int, default=1500, help="CPU-baseline sample size")

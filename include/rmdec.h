@@ -115,8 +115,8 @@ rmdec_status rmdec_set_hadamard(rmdec_t h, rmdec_hadamard mode);
  * AUTO (default): PATH where it exists, else WARP.
  * WARP: one warp per decoder, the L paths spread over its lanes and the tree's LLR buffers in
  *   shared memory; every supported code.
- * PATH: one thread per list path, the tree's LLRs in registers, the decoders of a frame in
- *   one lane group; RM(2, m) with 4 <= m <= 7 and L in {1, 2, 4, 8}, FP32 butterflies
+ * PATH: one thread per list path (two for m = 8), the tree's LLRs in registers, the decoders
+ *   of a frame in one lane group; RM(2, m) with 4 <= m <= 8 and L in {1, 2, 4, 8}, FP32 butterflies
  *   (RMDEC_EINVAL otherwise). Integer inputs decode identically under both; FP32 inputs may
  *   differ where two FHTL candidates of one path round to the same FP32 metric (WARP then
  *   prefers the smaller index, PATH the larger |c_k|). Decoders that run PATH decode their

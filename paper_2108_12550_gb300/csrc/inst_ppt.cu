@@ -1,4 +1,4 @@
-// Kernel instances of the path-per-thread decoder for RM(2, m), 4 <= m <= 7 (ppt_kernel.cuh).
+// Kernel instances of the path-per-thread decoder for RM(2, m), 4 <= m <= 8 (ppt_kernel.cuh).
 #include "ppt_kernel.cuh"
 #include "rmdec_internal.h"
 
@@ -37,6 +37,7 @@ bool lookup_pfht_ppt(int m, int r, int L, int P, KernelEntry* e) {
         case 5: return ppt_case<5>(L, P, e);
         case 6: return ppt_case<6>(L, P, e);
         case 7: return ppt_case<7>(L, P, e);
+        case 8: return ppt_case<8>(L, P, e);
     }
     return false;
 }

@@ -1,19 +1,22 @@
-// p-FHT-FSCL-L-M for the short codes RM(2, m), 4 <= m <= 7, with one thread per list path.
+// p-FHT-FSCL-L-M for the short codes RM(2, m), 4 <= m <= 8, with one thread per list path
+// (two threads per path for m = 8).
 //
 // Method: Doan, Hashemi, Gross, arXiv 2108.12550 — Algorithm 2 (the root is the one permuted
 // node of an RM(2, m) tree: 2L candidate permutations ranked by the reliability metric LM),
 // Algorithms 3-4 with Eq. (8) (FHTL nodes RM(1, s)), Eqs. (2)-(6) (the SPCL node RM(2, 3)) and
 // Algorithm 5 (the best of P decoders).
 //
-// Execution model. The L paths of one decoder are L consecutive lanes of a warp; a lane keeps
-// its path's LLRs of every pending tree level, its Walsh-Hadamard spectra and its decided bits
-// in registers (at most 2^(m-1) + 2^(m-2) floats), so the tree's f/g steps and butterflies run
-// without shuffles or shared memory and every lane does useful work. Lists interact only at
-// the leaves: the survivors are chosen by shuffles among the decoder's L lanes, and a new path
-// copies its parent's pending LLRs with one shuffle per value. The decoders of a frame occupy
-// a group of FW consecutive lanes (FW = L x decoders per batch, a power of two); a warp
-// decodes 32 / FW frames at once, their LLRs staged in the warp's own shared memory, and runs
-// the P decoders of each frame in batches of FW / L.
+// Execution model. The L paths of one decoder are G L consecutive lanes of a warp (G = 1 lane
+// per path, or G = 2 for m = 8: lane g of a path holds its positions i = G e + g); a lane keeps
+// its share of the path's LLRs of every pending tree level, the Walsh-Hadamard spectra and the
+// path's decided bits in registers (at most 64 + 32 floats), so the tree's f/g steps and
+// butterflies run without shared memory (for G = 2 one butterfly stage of each node pairs the
+// path's two lanes) and every lane does useful work. Lists interact only at the leaves: the
+// survivors are chosen by shuffles among the decoder's lanes, and a new path copies its
+// parent's pending LLRs with one shuffle per value. The decoders of a frame occupy a group of
+// FW consecutive lanes (FW = G L x decoders per batch, a power of two); a warp decodes 32 / FW
+// frames at once, their LLRs staged in the warp's own shared memory, and runs the P decoders of
+// each frame in batches of FW / (G L).
 //
 // Results: integer-valued inputs decode bit-exactly as the warp-per-decoder kernel and the
 // integer oracle do (every operation is exact there). Sums (the metric LM, sum |alpha| of an
@@ -30,18 +33,19 @@
 
 namespace rmdec_dev {
 
-// Lanes per frame group: the decoders of one batch (L lanes each); at least N / 32 lanes, so
+// Lanes per path: two for m = 8 (the largest leaf's 128 values), else one.
+__host__ __device__ constexpr int ppt_lanes_per_path(int m) { return m >= 8 ? 2 : 1; }
+// Lanes per frame group: the decoders of one batch (G L lanes each); at least N / 32 lanes, so
 // that a warp stages at most 32 N / FW <= 1024 LLRs (4 KB, plus the padding of ppt_frame_stride).
 __host__ __device__ constexpr int ppt_pow2_ceil(int x) { return x <= 1 ? 1 : 2 * ppt_pow2_ceil((x + 1) / 2); }
 __host__ __device__ inline int ppt_frame_lanes(int m, int L, int P) {
     const int n32 = m >= 5 ? (1 << m) / 32 : 1;
-    int fw = ppt_pow2_ceil(P * L);
+    int fw = ppt_pow2_ceil(P * L * ppt_lanes_per_path(m));
     if (fw > 32) fw = 32;
     if (fw < n32) fw = n32;
     return fw;
 }
 
-// trailing zeros of 0 < n < 128 (folds to a constant for constant n, unlike a recursion)
 // Floats between the starts of consecutive staged frames of a warp: N, padded when several
 // frames share the warp so that their starts fall on distinct banks, 32 / FPW banks apart (at
 // least 4, which keeps every frame 16-byte aligned for the vector loads).
@@ -51,11 +55,12 @@ __host__ __device__ inline int ppt_frame_stride(int m, int fpw) {
     const int spacing = 32 / fpw > 4 ? 32 / fpw : 4;
     return n + (((spacing - n) % 32) + 32) % 32;
 }
+// trailing zeros of 0 < n < 128 (folds to a constant for constant n, unlike a recursion)
 __host__ __device__ constexpr int ctz7(int n) {
     return (n & 1) ? 0 : (n & 2) ? 1 : (n & 4) ? 2 : (n & 8) ? 3 : (n & 16) ? 4 : (n & 32) ? 5 : 6;
 }
 
-// Word `idx` (< NW <= 4) of a register array, by a multiplexer on the index bits (an equality
+// Word `idx` (< NW <= 8) of a register array, by a multiplexer on the index bits (an equality
 // chain would be turned into a local-memory array by the compiler).
 template <int NW>
 __device__ __forceinline__ uint32_t pick_word(const uint32_t (&x)[NW], int idx) {
@@ -63,15 +68,22 @@ __device__ __forceinline__ uint32_t pick_word(const uint32_t (&x)[NW], int idx) 
         return x[0];
     } else if constexpr (NW == 2) {
         return (idx & 1) ? x[1] : x[0];
-    } else {
-        static_assert(NW == 4, "one to four words");
+    } else if constexpr (NW == 4) {
         const uint32_t lo = (idx & 1) ? x[1] : x[0], hi = (idx & 1) ? x[3] : x[2];
         return (idx & 2) ? hi : lo;
+    } else {
+        static_assert(NW == 8, "one to eight words");
+        const uint32_t a = (idx & 1) ? x[1] : x[0], b = (idx & 1) ? x[3] : x[2];
+        const uint32_t c = (idx & 1) ? x[5] : x[4], d = (idx & 1) ? x[7] : x[6];
+        const uint32_t lo = (idx & 2) ? b : a, hi = (idx & 2) ? d : c;
+        return (idx & 4) ? hi : lo;
     }
 }
 
 template <int M, int L>
 struct Ppt {
+    static constexpr int G = ppt_lanes_per_path(M);  // lanes per path
+    static constexpr int DL = G * L;                  // lanes per decoder
     static constexpr int N = 1 << M;
     static constexpr int H = N / 2;
     static constexpr int NW = (N + 31) / 32;
@@ -80,17 +92,19 @@ struct Ppt {
     // is decoded, instead of in registers: the register peak, and so the resident warps, then
     // follow the largest leaf alone.
     static constexpr bool PEND_SMEM = M >= 6;
-    static constexpr int PEND_FLOATS = PEND_SMEM ? H * 32 : 0;  // per warp
-    static_assert(M >= 4 && M <= 7, "short codes");
+    static constexpr int PEND_FLOATS = PEND_SMEM ? (H / G) * 32 : 0;  // per warp
+    static_assert(M >= 4 && M <= 8, "short codes");
     static_assert(L == 1 || L == 2 || L == 4 || L == 8, "list size");
+    static_assert(DL <= 32, "a decoder within a warp");
 
     struct Ctx {
         const float* y;         // the frame's LLRs (shared memory)
         const uint16_t* rec;    // the decoder's 2L composed root records (shared memory)
         uint8_t* sel;           // the warp's 32-byte selection scratch
-        float* pend;            // the warp's level-(m-1) LLRs: value i of lane t at [32 i + t]
+        float* pend;            // the warp's level-(m-1) LLRs: value e of lane t at [32 e + t]
         int dbase;              // lane of the decoder's path 0
         int l;                  // this lane's path
+        int g;                  // this lane within its path (positions G e + g)
         bool single;            // paths 1..L-1 start inactive (metric +inf)
     };
     struct Path {
@@ -101,6 +115,12 @@ struct Ppt {
 
     // bit i of the decided word
     __device__ __forceinline__ static unsigned bit(const Path& p, int i) { return (p.x[i >> 5] >> (i & 31)) & 1u; }
+    // bit G e + g, for a compile-time G e (the word is known; the lane's g shifts)
+    __device__ __forceinline__ static unsigned bitg(const Path& p, int ge, int g) {
+        return (p.x[ge >> 5] >> ((ge & 31) + g)) & 1u;
+    }
+    // the lane of path `path` holding this lane's positions
+    __device__ __forceinline__ static int lane_of(const Ctx& c, int path) { return c.dbase + G * path + c.g; }
 
     // Writes the NB bits `v` at span offset OFF (NB <= 32 and OFF a multiple of NB, or NB a
     // multiple of 32 with v holding word `wd`).
@@ -127,7 +147,7 @@ struct Ppt {
     // `pend` (PC values) and the decided bits left of span offset OFF.
     template <int OFF, int PC, int PA>
     __device__ __forceinline__ static void list_step(const Ctx& c, Path& p, int par, float (&pend)[PA]) {
-        const int src = c.dbase + par;
+        const int src = lane_of(c, par);
         p.rootc = __shfl_sync(kFull, p.rootc, src);
 #pragma unroll
         for (int i = 0; i < PC; i++) pend[i] = __shfl_sync(kFull, pend[i], src);
@@ -140,71 +160,85 @@ struct Ppt {
     // candidates (k, sign of c_k) with PM' = PM + (sum|alpha| - |c_k|) / 2; the L best over the
     // decoder's paths by (PM', path, k) survive. pend: the PC pending LLRs a new path copies.
     template <int S, int OFF, int PC, int PA>
-    __device__ __forceinline__ static int fht_leaf(const Ctx& c, Path& p, float (&v)[1 << S], float (&pend)[PA]) {
+    __device__ __forceinline__ static int fht_leaf(const Ctx& c, Path& p, float (&v)[(1 << S) / G], float (&pend)[PA]) {
         constexpr int NS = 1 << S;
-        constexpr int T = cmin(L, NS);
-        static_assert(T == L, "every path offers L candidates");
-        // the warp-per-decoder kernel's lanes per path (G) and values per lane (E): sums and
-        // butterflies below associate as its lane and register steps do
-        constexpr int G = cmin(32 / L, NS);
-        constexpr int E = NS / G;
+        constexpr int VS = NS / G;      // this lane's values: positions G e + g
+        constexpr int T = cmin(L, VS);  // candidates a lane offers (all of a path's L best)
+        // the warp-per-decoder kernel's lanes per path (GO) and values per lane (EO): sums and
+        // butterflies below associate as its lane and register steps do; its lane go holds
+        // positions go + GO eo, here in the lane g = go mod G, at e = go / G + (GO / G) eo
+        constexpr int GO = cmin(32 / L, NS);
+        constexpr int EO = NS / GO;
+        constexpr int HO = GO / G;  // its lanes whose positions this lane holds
+        static_assert(GO % G == 0, "whole lanes of that kernel per lane");
         float A;
         {
-            float tg[G];
+            float tg[HO];
 #pragma unroll
-            for (int g = 0; g < G; g++) {
-                float t[E];
+            for (int ho = 0; ho < HO; ho++) {
+                float t[EO];
 #pragma unroll
-                for (int e = 0; e < E; e++) t[e] = fabsf(v[g + G * e]);
+                for (int e = 0; e < EO; e++) t[e] = fabsf(v[ho + HO * e]);
 #pragma unroll
-                for (int h = E / 2; h >= 1; h >>= 1)
+                for (int h = EO / 2; h >= 1; h >>= 1)
 #pragma unroll
                     for (int e = 0; e < h; e++) t[e] += t[e + h];
-                tg[g] = t[0];
+                tg[ho] = t[0];
+            }
+            if constexpr (G == 2) {
+#pragma unroll
+                for (int ho = 0; ho < HO; ho++) tg[ho] += __shfl_xor_sync(kFull, tg[ho], 1);
             }
 #pragma unroll
-            for (int d = 1; d < G; d <<= 1)
+            for (int d = 1; d < HO; d <<= 1)
 #pragma unroll
-                for (int g = 0; g < G; g += 2 * d) tg[g] += tg[g + d];
+                for (int ho = 0; ho < HO; ho += 2 * d) tg[ho] += tg[ho + d];
             A = tg[0];
         }
-        // butterflies (u, w) -> (u + w, u - w): index bits of e, then of g
+        // butterflies (u, w) -> (u + w, u - w): index bits of eo, then of go
 #pragma unroll
-        for (int h = 1; h < E; h <<= 1)
+        for (int h = 1; h < EO; h <<= 1)
 #pragma unroll
-            for (int e = 0; e < E; e++)
+            for (int e = 0; e < EO; e++)
                 if (!(e & h))
 #pragma unroll
-                    for (int g = 0; g < G; g++) {
-                        const float a = v[g + G * e], b = v[g + G * (e + h)];
-                        v[g + G * e] = a + b;
-                        v[g + G * (e + h)] = a - b;
+                    for (int ho = 0; ho < HO; ho++) {
+                        const float a = v[ho + HO * e], b = v[ho + HO * (e + h)];
+                        v[ho + HO * e] = a + b;
+                        v[ho + HO * (e + h)] = a - b;
                     }
 #pragma unroll
-        for (int d = 1; d < G; d <<= 1)
+        for (int d = 1; d < GO; d <<= 1) {
+            if (d < G) {
+                // positions i and i ^ 1 sit in the path's two lanes: lower u + w, upper u - w
+                const float sg = c.g ? -1.f : 1.f;
 #pragma unroll
-            for (int g = 0; g < G; g++)
-                if (!(g & d))
+                for (int e = 0; e < VS; e++) v[e] = fmaf(sg, v[e], __shfl_xor_sync(kFull, v[e], 1));
+            } else {
+                const int dl = d / G;
 #pragma unroll
-                    for (int e = 0; e < E; e++) {
-                        const float a = v[g + G * e], b = v[(g | d) + G * e];
-                        v[g + G * e] = a + b;
-                        v[(g | d) + G * e] = a - b;
+                for (int e = 0; e < VS; e++)
+                    if (((e % HO) & dl) == 0) {
+                        const float a = v[e], b = v[e + dl];
+                        v[e] = a + b;
+                        v[e + dl] = a - b;
                     }
-        // the path's T best candidates by (|c_k| descending, k ascending): a scan in k order
-        // inserts before the first entry of strictly smaller |c|; entries hold |c| (sentinel
-        // -1) and 2k + [c_k < 0]
+            }
+        }
+        // this lane's T best candidates by (|c_k| descending, k ascending): a scan in k order
+        // (k = G e + g) inserts before the first entry of strictly smaller |c|; entries hold |c|
+        // (sentinel -1) and 2k + [c_k < 0]
         float tv[T];
         unsigned tk[T];
 #pragma unroll
         for (int j = 0; j < T; j++) {
             tv[j] = -1.f;
-            tk[j] = 2u * j;
+            tk[j] = 2u * (G * j + c.g);
         }
 #pragma unroll
-        for (int k = 0; k < NS; k++) {
-            const float x = fabsf(v[k]);
-            const unsigned xk = 2u * k + (v[k] < 0.f ? 1u : 0u);
+        for (int e = 0; e < VS; e++) {
+            const float x = fabsf(v[e]);
+            const unsigned xk = 2u * (G * e + c.g) + (v[e] < 0.f ? 1u : 0u);
             // the new list from the old one: entry j keeps, takes x, or takes entry j - 1
             bool gt[T];
 #pragma unroll
@@ -224,7 +258,7 @@ struct Ppt {
                 tk[j] = ntk[j];
             }
         }
-        // keys (PM', path 2^(S+1) + 2k + sign) of the path's list, in ascending order
+        // keys (PM', path 2^(S+1) + 2k + sign) of the lane's list, in ascending order
         unsigned key[T], cid[T];
 #pragma unroll
         for (int j = 0; j < T; j++) {
@@ -232,14 +266,14 @@ struct Ppt {
             cid[j] = ((unsigned)c.l << (S + 1)) | tk[j];
         }
         unsigned mkey = key[0], mcid = cid[0];
-        if constexpr (L > 1) {
+        if constexpr (DL > 1) {
             // L rounds of the decoder-wide minimum of the lanes' heads; round q's winner
             // becomes path q
 #pragma unroll
             for (int q = 0; q < L; q++) {
                 unsigned bk = key[0], bc = cid[0];
 #pragma unroll
-                for (int d = 1; d < L; d <<= 1) {
+                for (int d = 1; d < DL; d <<= 1) {
                     const unsigned ok = __shfl_xor_sync(kFull, bk, d);
                     const unsigned oc = __shfl_xor_sync(kFull, bc, d);
                     const bool take = ok < bk || (ok == bk && oc < bc);
@@ -256,6 +290,8 @@ struct Ppt {
                         key[j] = key[j + 1];
                         cid[j] = cid[j + 1];
                     }
+                    key[T - 1] = 0xffffffffu;  // an exhausted list offers nothing
+                    cid[T - 1] = 0xffffffffu;
                 }
             }
         }
@@ -290,9 +326,23 @@ struct Ppt {
     // splits on the next least reliable positions (flip cost |alpha_i| + (1-2p)|alpha_lrb|, each
     // a 2L -> L selection by (PM, 2 path + flip)); the least reliable bit restores even parity.
     template <int OFF>
-    __device__ __forceinline__ static void spc_leaf(const Ctx& c, Path& p, float (&a)[8]) {
+    __device__ __forceinline__ static void spc_leaf(const Ctx& c, Path& p, float (&as)[8 / G]) {
         constexpr int NS = 8;
         constexpr int TAU = cmin(L, NS - 1);
+        // the node's 8 LLRs in every lane of the path (both lanes of a path then hold the same
+        // state and take the same decisions; shuffles read a path's lane g = 0)
+        float a[NS];
+        if constexpr (G == 1) {
+#pragma unroll
+            for (int i = 0; i < NS; i++) a[i] = as[i];
+        } else {
+#pragma unroll
+            for (int e = 0; e < NS / G; e++) {
+                const float o = __shfl_xor_sync(kFull, as[e], 1);
+                a[G * e] = c.g ? o : as[e];
+                a[G * e + 1] = c.g ? as[e] : o;
+            }
+        }
         // reliability order (|alpha|, position) ascending: Batcher's odd-even merge sort network
         float sv[NS];
         int sp[NS];
@@ -335,7 +385,7 @@ struct Ppt {
 #pragma unroll 1
         for (int t = 1; t <= TAU; t++) {
             // the split position and the LRB belong to the path's SPC-entry ancestor `orig`
-            const int so = c.dbase + orig;
+            const int so = c.dbase + G * orig;
             const float r_o = __shfl_sync(kFull, rel[0], so);
             const int itp = __shfl_sync(kFull, pos[0], so);
             const float lrb_o = __shfl_sync(kFull, lrb, so);
@@ -344,20 +394,20 @@ struct Ppt {
             int rk = 0, rf = 0;
 #pragma unroll
             for (int l2 = 0; l2 < L; l2++) {
-                const float k2 = __shfl_sync(kFull, pm, c.dbase + l2);
-                const float f2 = __shfl_sync(kFull, pflip, c.dbase + l2);
+                const float k2 = __shfl_sync(kFull, pm, c.dbase + G * l2);
+                const float f2 = __shfl_sync(kFull, pflip, c.dbase + G * l2);
                 rk += (k2 < pm) || (k2 == pm && l2 < c.l);
                 rk += (f2 < pm) || (f2 == pm && l2 < c.l);
                 rf += (k2 < pflip) || (k2 == pflip && l2 <= c.l);
                 rf += (f2 < pflip) || (f2 == pflip && l2 < c.l);
             }
             // the candidate of rank q becomes path q
-            if (rk < L) c.sel[c.dbase + rk] = (uint8_t)(2 * c.l);
-            if (rf < L) c.sel[c.dbase + rf] = (uint8_t)(2 * c.l + 1);
+            if (c.g == 0 && rk < L) c.sel[c.dbase + rk] = (uint8_t)(2 * c.l);
+            if (c.g == 0 && rf < L) c.sel[c.dbase + rf] = (uint8_t)(2 * c.l + 1);
             __syncwarp();
             const int mysrc = c.sel[c.dbase + c.l];
             __syncwarp();
-            const int sl = c.dbase + ((mysrc >> 1) & (L - 1));
+            const int sl = c.dbase + G * ((mysrc >> 1) & (L - 1));
             const bool fl = mysrc & 1;
             const float n_kpm = __shfl_sync(kFull, pm, sl);
             const float n_fpm = __shfl_sync(kFull, pflip, sl);
@@ -374,7 +424,7 @@ struct Ppt {
                 pos[k] = pos[k + 1];
             }
         }
-        const int so = c.dbase + orig;
+        const int so = c.dbase + G * orig;
         const unsigned hd_o = __shfl_sync(kFull, hd, so);
         const int lo0 = __shfl_sync(kFull, o0, so) & (NS - 1);
         unsigned x = ((hd_o ^ flip) & 0xffu) & ~(1u << lo0);
@@ -388,32 +438,33 @@ struct Ppt {
     // ------------------------------------------------------------- tree walk ---
     // RM(2, S) node off the root (not permuted), LLRs `a`, at span offset OFF
     template <int S, int OFF>
-    __device__ __forceinline__ static void node2(const Ctx& c, Path& p, float (&a)[1 << S]) {
+    __device__ __forceinline__ static void node2(const Ctx& c, Path& p, float (&a)[(1 << S) / G]) {
         if constexpr (S == 3) {
             spc_leaf<OFF>(c, p, a);
         } else {
             constexpr int HS = 1 << (S - 1);
-            float ch[HS];
+            constexpr int VH = HS / G;  // this lane's share of a child's positions
+            float ch[VH];
             if constexpr (PEND_SMEM && S == M - 1) {
                 // park the node's LLRs in this lane's column; the new path reads its parent's
-                const int lane = c.dbase + c.l;
+                const int lane = c.dbase + G * c.l + c.g;
                 __syncwarp();  // every lane has read the previous decoder's columns
 #pragma unroll
-                for (int i = 0; i < (1 << S); i++) c.pend[32 * i + lane] = a[i];
+                for (int e = 0; e < 2 * VH; e++) c.pend[32 * e + lane] = a[e];
                 __syncwarp();
 #pragma unroll
-                for (int i = 0; i < HS; i++) ch[i] = fminsum(a[i], a[i + HS]);
+                for (int e = 0; e < VH; e++) ch[e] = fminsum(a[e], a[e + VH]);
                 float none[1];
                 const int par = fht_leaf<S - 1, OFF, 0>(c, p, ch, none);
-                const float* pa = c.pend + c.dbase + par;
+                const float* pa = c.pend + lane_of(c, par);
 #pragma unroll
-                for (int i = 0; i < HS; i++) ch[i] = g_fn(pa[32 * i], pa[32 * (i + HS)], bit(p, OFF + i));
+                for (int e = 0; e < VH; e++) ch[e] = g_fn(pa[32 * e], pa[32 * (e + VH)], bitg(p, OFF + G * e, c.g));
             } else {
 #pragma unroll
-                for (int i = 0; i < HS; i++) ch[i] = fminsum(a[i], a[i + HS]);
-                fht_leaf<S - 1, OFF, 1 << S>(c, p, ch, a);
+                for (int e = 0; e < VH; e++) ch[e] = fminsum(a[e], a[e + VH]);
+                fht_leaf<S - 1, OFF, 2 * VH>(c, p, ch, a);
 #pragma unroll
-                for (int i = 0; i < HS; i++) ch[i] = g_fn(a[i], a[i + HS], bit(p, OFF + i));
+                for (int e = 0; e < VH; e++) ch[e] = g_fn(a[e], a[e + VH], bitg(p, OFF + G * e, c.g));
             }
             node2<S - 1, OFF + HS>(c, p, ch);
             combine<OFF, HS>(p);
@@ -426,29 +477,34 @@ struct Ppt {
     // reduction do. Returns this path's candidate: the one of rank l by (LM desc, c asc).
     __device__ __forceinline__ static int select_root(const Ctx& c) {
         constexpr int V = H < 32 ? H : 32;  // lanes of that kernel holding pairs
+        static_assert(V % G == 0, "its lanes split evenly over a path's lanes");
+        constexpr int VL = V / G;            // of them, the ones this lane sums: lv = G u + g
         float lm[2];
 #pragma unroll
         for (int q = 0; q < 2; q++) {
             const uint16_t* r = c.rec + (c.l + q * L) * kRec;
             const int a = r[M - 1];
             const int hm = ~((1 << (31 - __clz(a))) - 1);  // index bits at and above bit msb(a)
-            float acc[V];
+            float acc[VL];
 #pragma unroll
-            for (int lv = 0; lv < V; lv++) {
+            for (int u = 0; u < VL; u++) {
                 float s = 0.f;
 #pragma unroll
                 for (int t = 0; t < (H + 31) / 32; t++) {
-                    const int jp = lv + 32 * t;  // the pair's representative: bit msb(a) clear
+                    const int jp = G * u + c.g + 32 * t;  // the pair's representative: bit msb(a) clear
                     const int j = jp + (jp & hm);
                     s += fminf(fabsf(c.y[j]), fabsf(c.y[j ^ a]));
                 }
-                acc[lv] = s;
+                acc[u] = s;
             }
+            // that kernel's warp sum, d = 16, 8, ..., 1: the steps d >= G within this lane, then
+            // (G = 2) d = 1 between the path's two lanes
 #pragma unroll
-            for (int d = 16; d >= 1; d >>= 1)
+            for (int d = 16; d >= G; d >>= 1)
 #pragma unroll
-                for (int lv = 0; lv < d; lv++)
-                    if (lv + d < V) acc[lv] += acc[lv + d];
+                for (int u = 0; u < d / G; u++)
+                    if (u + d / G < VL) acc[u] += acc[u + d / G];
+            if constexpr (G == 2) acc[0] += __shfl_xor_sync(kFull, acc[0], 1);
             lm[q] = acc[0];
         }
         if constexpr (L == 1) {
@@ -459,7 +515,7 @@ struct Ppt {
             for (int l2 = 0; l2 < L; l2++) {
 #pragma unroll
                 for (int q2 = 0; q2 < 2; q2++) {
-                    const float o = __shfl_sync(kFull, lm[q2], c.dbase + l2);
+                    const float o = __shfl_sync(kFull, lm[q2], c.dbase + G * l2);
                     const int c2 = l2 + q2 * L;
 #pragma unroll
                     for (int q = 0; q < 2; q++) {
@@ -470,7 +526,7 @@ struct Ppt {
             }
 #pragma unroll
             for (int q = 0; q < 2; q++)
-                if (rk[q] < L) c.sel[c.dbase + rk[q]] = (uint8_t)(c.l + q * L);
+                if (c.g == 0 && rk[q] < L) c.sel[c.dbase + rk[q]] = (uint8_t)(c.l + q * L);
             __syncwarp();
             const int mine = c.sel[c.dbase + c.l] & (2 * L - 1);
             __syncwarp();
@@ -485,7 +541,9 @@ struct Ppt {
         p.pm = (c.single && (p.rootc & (L - 1)) != 0) ? __int_as_float(0x7f800000) : 0.f;
 #pragma unroll
         for (int w = 0; w < NW; w++) p.x[w] = 0;
-        float a[H];
+        constexpr int VH = H / G;  // this lane's positions of a root child: G e + g
+        constexpr int LG = G == 2 ? 1 : 0;
+        float a[VH];
         int col[M - 1];
         int sb, sa;
         auto load_rec = [&]() {
@@ -493,18 +551,18 @@ struct Ppt {
 #pragma unroll
             for (int t = 0; t < M - 1; t++) col[t] = r[t];
             sa = r[M - 1];
-            sb = r[10];
+            sb = r[10] ^ ((G == 2 && c.g) ? col[0] : 0);  // the image of position g
         };
-        // f: left child RM(1, m-1) from y through the path's root permutation, positions in
-        // Gray-code order (one XOR per position)
+        // f: left child RM(1, m-1) from y through the path's root permutation, this lane's
+        // positions in Gray-code order of e (one XOR per position)
         load_rec();
         {
             int s = sb;
 #pragma unroll
-            for (int n = 0; n < H; n++) {
-                if (n) s ^= col[ctz7(n)];
-                const int i = n ^ (n >> 1);
-                a[i] = fminsum(c.y[s], c.y[s ^ sa]);
+            for (int n = 0; n < VH; n++) {
+                if (n) s ^= col[LG + ctz7(n)];
+                const int e = n ^ (n >> 1);
+                a[e] = fminsum(c.y[s], c.y[s ^ sa]);
             }
         }
         float none[1];
@@ -514,10 +572,10 @@ struct Ppt {
         {
             int s = sb;
 #pragma unroll
-            for (int n = 0; n < H; n++) {
-                if (n) s ^= col[ctz7(n)];
-                const int i = n ^ (n >> 1);
-                a[i] = g_fn(c.y[s], c.y[s ^ sa], bit(p, i));
+            for (int n = 0; n < VH; n++) {
+                if (n) s ^= col[LG + ctz7(n)];
+                const int e = n ^ (n >> 1);
+                a[e] = g_fn(c.y[s], c.y[s ^ sa], bitg(p, G * e, c.g));
             }
         }
         node2<M - 1, H>(c, p, a);
@@ -533,9 +591,9 @@ __host__ __device__ constexpr int ppt_min_blocks(int m) { return m >= 6 ? 3 : 5;
 template <int M, int L>
 __global__ void __launch_bounds__(128, ppt_min_blocks(M)) ppt_kernel(LaunchArgs a) {
     using D = Ppt<M, L>;
-    constexpr int N = D::N, NW = D::NW, NREC = D::NREC;
+    constexpr int N = D::N, NW = D::NW, NREC = D::NREC, DL = D::DL;
     constexpr int K = 1 + M + M * (M - 1) / 2;  // information bits of RM(2, m)
-    static_assert(K <= 32, "one information word");
+    constexpr int KW = (K + 31) / 32;
     extern __shared__ __align__(16) uint8_t smem[];
     const int FW = ppt_frame_lanes(M, L, a.P);
     const int FPW = 32 / FW;
@@ -556,14 +614,15 @@ __global__ void __launch_bounds__(128, ppt_min_blocks(M)) ppt_kernel(LaunchArgs 
     float* s_y = s_pend + D::PEND_FLOATS;
     uint8_t* s_sel = smem + tables + warp * warp_bytes + (D::PEND_FLOATS + FPW * YS) * 4;
     const int grp = lane / FW, j = lane % FW, gbase = grp * FW;
-    const int DPB = FW / L;  // decoders per batch
-    const int ds = j / L;
+    const int DPB = FW / DL;  // decoders per batch
+    const int ds = j / DL;
     typename D::Ctx c;
     c.y = s_y + grp * YS;
     c.sel = s_sel;
     c.pend = s_pend;
-    c.dbase = gbase + ds * L;
-    c.l = j % L;
+    c.dbase = gbase + ds * DL;
+    c.l = (j % DL) / D::G;
+    c.g = j % D::G;
     c.single = a.single_start != 0;
     const unsigned gmask = FW == 32 ? 0xffffffffu : ((1u << FW) - 1u);
     const size_t eb = a.dtype == IN_F32 ? 4 : (a.dtype == IN_I8 ? 1 : 2);
@@ -629,7 +688,7 @@ __global__ void __launch_bounds__(128, ppt_min_blocks(M)) ppt_kernel(LaunchArgs 
             const float v = p.pm == p.pm ? p.pm : __int_as_float(0x7f800000);
             unsigned bk = dvalid ? ordered_bits(v) : 0xffffffffu;
             unsigned bd = (unsigned)ds;
-            for (int dl = L; dl < FW; dl <<= 1) {
+            for (int dl = DL; dl < FW; dl <<= 1) {
                 const unsigned ok = __shfl_xor_sync(kFull, bk, dl);
                 const unsigned od = __shfl_xor_sync(kFull, bd, dl);
                 const bool take = ok < bk || (ok == bk && od < bd);
@@ -638,7 +697,7 @@ __global__ void __launch_bounds__(128, ppt_min_blocks(M)) ppt_kernel(LaunchArgs 
             }
             bk = __shfl_sync(kFull, bk, gbase);
             bd = __shfl_sync(kFull, bd, gbase);
-            const int wl = gbase + (int)bd * L;
+            const int wl = gbase + (int)bd * DL;
             uint32_t xw[NW];
 #pragma unroll
             for (int w = 0; w < NW; w++) xw[w] = __shfl_sync(kFull, p.x[w], wl);
@@ -703,17 +762,21 @@ __global__ void __launch_bounds__(128, ppt_min_blocks(M)) ppt_kernel(LaunchArgs 
             for (int w = 0; w < NW; w++)
                 if (!(w & dd)) u[w] ^= u[w | dd];
         }
-        unsigned iw = 0;
-        for (int t = 0; t * FW < K; t++) {
-            const int q = j + FW * t;
-            unsigned b = 0;
-            if (q < K) {
-                const int pos = s_info[q];
-                b = (pick_word(u, pos >> 5) >> (pos & 31)) & 1u;
+        uint32_t iw[KW];
+#pragma unroll
+        for (int w = 0; w < KW; w++) {  // information word w: FW positions per ballot
+            iw[w] = 0;
+            for (int o = 0; o < 32 && 32 * w + o < K; o += FW) {
+                const int q = 32 * w + o + j;
+                unsigned b = 0;
+                if (q < K) {
+                    const int pos = s_info[q];
+                    b = (pick_word(u, pos >> 5) >> (pos & 31)) & 1u;
+                }
+                iw[w] |= ((__ballot_sync(kFull, b) >> gbase) & gmask) << o;
             }
-            iw |= ((__ballot_sync(kFull, b) >> gbase) & gmask) << ((FW * t) & 31);
         }
-        if (fvalid && j == 0) a.info_out[f] = iw;
+        if (fvalid && j < KW) a.info_out[f * KW + j] = pick_word(iw, j);
     }
 }
 

@@ -44,7 +44,7 @@ bool lookup_pfht_l32_small(int m, int r, KernelEntry* e);  // m = 4 .. 7
 bool lookup_pfht_l32_m8(int r, KernelEntry* e);
 bool lookup_pfht_l32_m9(int r, KernelEntry* e);
 
-// Path-per-thread kernels for RM(2, m), 4 <= m <= 7, L in {1, 2, 4, 8} (inst_ppt.cu); the
+// Path-per-thread kernels for RM(2, m), 4 <= m <= 8, L in {1, 2, 4, 8} (inst_ppt.cu); the
 // entry's shared-memory sizes depend on the decoder count P.
 bool lookup_pfht_ppt(int m, int r, int L, int P, KernelEntry* e);
 

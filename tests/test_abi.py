@@ -147,3 +147,4 @@ def test_kernel_choice_is_checked_on_the_host():
         assert ei.value.status == pkg.EINVAL
     assert d._lib.rmdec_set_kernel(d._h, 7) == pkg.EINVAL
     pkg.Decoder(4, 2, 128, 8).set_kernel("path")
+    pkg.Decoder(8, 2, 20, 8).set_kernel("path")

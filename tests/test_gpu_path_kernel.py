@@ -1,4 +1,5 @@
-"""The path-per-thread kernel (one thread per list path, RM(2, m) with 4 <= m <= 7, L <= 8)
+"""The path-per-thread kernel (one thread per list path, two for m = 8; RM(2, m) with
+4 <= m <= 8, L <= 8)
 against the warp-per-decoder kernel and the oracle, through the C ABI.
 
 Both kernels run the same method (Algorithms 2-5), so on integer LLRs (INT8, INT16, FP32
@@ -34,7 +35,7 @@ def _both(m, r, P, L, x, dtype, perms):
 
 # (m, P, L, frames): every list size, batches of decoders (P * L > 32), idle decoder slots
 # (P * L not a power of two) and ragged frame counts (not a multiple of the frames per warp)
-CASES = [(m, P, L, nf) for m in (4, 5, 6, 7) for (P, L, nf) in
+CASES = [(m, P, L, nf) for m in (4, 5, 6, 7, 8) for (P, L, nf) in
          [(1, 1, 333), (3, 2, 250), (8, 4, 200), (20, 4, 61), (2, 8, 97), (5, 8, 33)]]
 
 
@@ -49,7 +50,7 @@ def test_integer_llrs_identical_to_the_warp_kernel(m, P, L, nf):
         assert np.array_equal(a, b), name
 
 
-@pytest.mark.parametrize("m,P,L", [(5, 4, 2), (7, 8, 4), (6, 3, 8), (4, 2, 1)])
+@pytest.mark.parametrize("m,P,L", [(5, 4, 2), (7, 8, 4), (6, 3, 8), (4, 2, 1), (8, 8, 4), (8, 3, 8), (8, 2, 1)])
 def test_integer_llrs_match_the_oracle(m, P, L):
     r = 2
     fr = I.make_frames(m, r, 300, 2.0, seed=70 + m)
@@ -65,7 +66,7 @@ def test_integer_llrs_match_the_oracle(m, P, L):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f16", "i16"])
-@pytest.mark.parametrize("m,P,L", [(5, 4, 2), (7, 8, 4), (6, 20, 8)])
+@pytest.mark.parametrize("m,P,L", [(5, 4, 2), (7, 8, 4), (6, 20, 8), (8, 20, 4)])
 def test_other_input_types_agree_with_the_warp_kernel(m, P, L, dtype):
     r = 2
     fr = I.make_frames(m, r, 1500, 2.5, seed=90 + m + L)
@@ -116,6 +117,7 @@ def test_tuning_shapes_and_tiny_batches():
 def test_kernel_choice_is_validated():
     with pytest.raises(pkg.RmdecError):
         pkg.Decoder(9, 2, 4, 4).set_kernel("path")  # no path-per-thread kernel for m = 9
+    pkg.Decoder(8, 2, 20, 8).set_kernel("path")
     with pytest.raises(pkg.RmdecError):
         pkg.Decoder(6, 3, 4, 4).set_kernel("path")  # nor for r = 3
     with pytest.raises(pkg.RmdecError):

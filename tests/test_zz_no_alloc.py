@@ -77,7 +77,7 @@ def test_noalloc_decode_with_the_path_per_thread_kernel():
     torch = pytest.importorskip("torch")
     lib = pkg.load_library()
     stream = torch.cuda.current_stream().cuda_stream
-    for (m, P, L, dt, nf) in [(7, 8, 4, "i8", 501), (5, 4, 2, "f32", 333)]:
+    for (m, P, L, dt, nf) in [(7, 8, 4, "i8", 501), (5, 4, 2, "f32", 333), (8, 8, 4, "f32", 257)]:
         d = pkg.Decoder(m, 2, P, L, perm_seed=21, dtype=dt)
         fr = I.make_frames(m, 2, nf, 2.5, seed=40 + m)
         x = fr["llr"].astype(np.float32) if dt == "f32" else I.quantize_i8(fr["llr"])
