@@ -112,15 +112,17 @@ typedef enum {
 rmdec_status rmdec_set_hadamard(rmdec_t h, rmdec_hadamard mode);
 
 /* Which kernel runs a p-FHT-FSCL decode (Algorithms 2-5; the same method either way).
- * AUTO (default): PATH where it exists, else WARP.
+ * AUTO (default): WARP, and PATH for launches of at least 512 (m <= 5), 2,048 (m = 6, 7) or
+ *   8,192 (m = 8) frames where it exists (measured crossovers: the warp kernel answers small
+ *   launches sooner, the path kernel has the higher throughput).
  * WARP: one warp per decoder, the L paths spread over its lanes and the tree's LLR buffers in
  *   shared memory; every supported code.
  * PATH: one thread per list path (two for m = 8), the tree's LLRs in registers, the decoders
  *   of a frame in one lane group; RM(2, m) with 4 <= m <= 8 and L in {1, 2, 4, 8}, FP32 butterflies
  *   (RMDEC_EINVAL otherwise). Integer inputs decode identically under both; FP32 inputs may
  *   differ where two FHTL candidates of one path round to the same FP32 metric (WARP then
- *   prefers the smaller index, PATH the larger |c_k|). Decoders that run PATH decode their
- *   segments of a grouped launch in their own launch (rmdec_group.h). */
+ *   prefers the smaller index, PATH the larger |c_k|). Segments of a grouped launch that
+ *   their decoder's own launch would give to PATH are decoded in that launch (rmdec_group.h). */
 typedef enum {
     RMDEC_KERNEL_AUTO = 0,
     RMDEC_KERNEL_WARP = 1,
@@ -195,8 +197,9 @@ rmdec_status rmdec_poll(rmdec_t h, uint64_t ticket, int64_t timeout_us);
 
 /* Launch shape: warps per CTA (1..20, at most P; Aut-SSC handles use at most 4; the decoders
  * of a frame are split across a CTA's warps; path-per-thread kernels (rmdec_set_kernel) take
- * 1..4 warps, each decoding its own frames) and a cap on resident CTAs per SM (0 = the
- * occupancy limit); 0 warps = the default: for p-FHT-FSCL kernels whose CTA decodes one frame,
+ * 1..4 warps, which split the decoder batches of the CTA's frames) and a cap on resident CTAs per SM (0 = the
+ * occupancy limit); 0 warps = the default: for path-per-thread kernels one warp per decoder
+ * batch of a frame (up to four); for p-FHT-FSCL kernels whose CTA decodes one frame,
  * 4 (else 3, else 2) warps when that splits the P decoders evenly and keeps at least two thirds
  * of the most resident warps per SM; otherwise the most resident warps per SM, then warps that
  * split the P decoders evenly, then two or more decoders per warp and two or more CTAs per

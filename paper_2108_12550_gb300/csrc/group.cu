@@ -280,9 +280,10 @@ rmdec_status rmdec_group_decode(rmdec_group_t g, const rmdec_segment* segs, int 
     }
     // Segments that fill at least min_alone frames (default: half a wave of their decoder's
     // own launch) run in their decoder's own kernel, which keeps its own register and
-    // shared-memory footprint, and so do all segments of decoders that run the path-per-thread
-    // kernel (the grouped kernel is the warp-per-decoder one, whose FP32 results may differ
-    // from it in rounding ties); the rest share grouped launches, most work per frame first
+    // shared-memory footprint, and so do the segments that their decoder's own launch would give
+    // to the path-per-thread kernel (the grouped kernel is the warp-per-decoder one, whose FP32
+    // results may differ from it in rounding ties); the rest share grouped launches, most work
+    // per frame first
     // (stable, so equal costs keep the caller's order). Measured on four codes at 600 frames
     // each (0.2 to 1.3 waves): a one-wave threshold 0.335 ms, half a wave 0.280 ms, a quarter
     // 0.274 ms but 20% slower at 200 frames each; separate launches 0.262 ms.
@@ -290,7 +291,8 @@ rmdec_status rmdec_group_decode(rmdec_group_t g, const rmdec_segment* segs, int 
     for (int i = 0; i < n_segs; i++) {
         if (segs[i].n_frames == 0) continue;
         const int64_t thr = g->min_alone > 0 ? g->min_alone : (mi[segs[i].decoder].wave + 1) / 2;
-        if (mi[segs[i].decoder].path_kernel || (g->min_alone >= 0 && segs[i].n_frames >= thr)) alone.push_back(i);
+        const int64_t pmin = mi[segs[i].decoder].path_min_frames;
+        if ((pmin >= 0 && segs[i].n_frames >= pmin) || (g->min_alone >= 0 && segs[i].n_frames >= thr)) alone.push_back(i);
         else order.push_back(i);
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -10,11 +10,20 @@ bool ppt_entry(int P, KernelEntry* e) {
     using D = rmdec_dev::Ppt<M, L>;
     const int fw = rmdec_dev::ppt_frame_lanes(M, L, P);
     e->fn = reinterpret_cast<const void*>(&rmdec_dev::ppt_kernel<M, L>);
-    e->frames_per_warp = 32 / fw;
-    e->warp_bytes = (D::PEND_FLOATS + e->frames_per_warp * rmdec_dev::ppt_frame_stride(M, e->frames_per_warp)) * 4 + 32;
+    e->frames_per_warp = 32 / fw;  // frames a CTA stages at a time
+    const int per_batch = fw / D::DL;
+    e->batches = (P + per_batch - 1) / per_batch;
+    // Smallest launch this kernel takes by default (the warp-per-decoder kernel takes smaller
+    // ones): where it overtook that kernel, measured with CUDA events over 64..65,536 frames
+    // (FP32, L = 4 unless stated): RM(2,5) P=4 L=2 from 512 frames, RM(2,6) P=8 and RM(2,7) P=8
+    // INT8 / P=20 from 2,048, RM(2,8) P=8 / P=20 from 8,192.
+    e->min_frames = M <= 5 ? 512 : (M <= 7 ? 2048 : 8192);
+    e->warp_bytes = D::PEND_FLOATS * 4 + 32 + rmdec_dev::kPptSlotWords * 4;
     e->nrec = 0;  // the maps sit in the fixed part
     e->fixed_bytes = [](int P2, int K, int) {
-        return ((P2 * 2 * rmdec_dev::Ppt<M, L>::NREC * rmdec_dev::kRec * 2 + K * 2) + 15) / 16 * 16;
+        const int fpw = 32 / rmdec_dev::ppt_frame_lanes(M, L, P2);
+        const int tables = ((P2 * 2 * rmdec_dev::Ppt<M, L>::NREC * rmdec_dev::kRec * 2 + K * 2) + 15) / 16 * 16;
+        return tables + ((fpw * rmdec_dev::ppt_frame_stride(M, fpw) * 4) + 15) / 16 * 16;
     };
     return true;
 }

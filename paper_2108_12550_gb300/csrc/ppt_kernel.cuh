@@ -15,8 +15,10 @@
 // survivors are chosen by shuffles among the decoder's lanes, and a new path copies its
 // parent's pending LLRs with one shuffle per value. The decoders of a frame occupy a group of
 // FW consecutive lanes (FW = G L x decoders per batch, a power of two); a warp decodes 32 / FW
-// frames at once, their LLRs staged in the warp's own shared memory, and runs the P decoders of
-// each frame in batches of FW / (G L).
+// frames at once and runs the P decoders of each frame in batches of FW / (G L). A CTA of W
+// warps takes 32 / FW frames at a time, staged once in its shared memory: warp w runs batches
+// w, w + W, ..., and the warps' best decoders meet in shared memory, so that a frame waits for
+// ceil(batches / W) batches rather than for all of them.
 //
 // Results: integer-valued inputs decode bit-exactly as the warp-per-decoder kernel and the
 // integer oracle do (every operation is exact there). Sums (the metric LM, sum |alpha| of an
@@ -583,6 +585,10 @@ struct Ppt {
 };
 
 // Decodes the frames of the job, one warp per 32 / FW frames (see Ppt).
+// Words of a warp's reduction slots: per staged frame its best decoder's metric key, index and
+// metric, and the decoder's codeword (32 / FW frames of 3 + N / 32 words; at most 128 words).
+constexpr int kPptSlotWords = 128;
+
 // Resident CTAs of 4 warps the register budget is sized for: 168 registers per thread for
 // m >= 6 (measured on RM(2,7) P=8 L=4: 79.0 M frames/s, against 71.0 M at 128 registers, where
 // the largest leaf spills), 102 for shorter codes.
@@ -600,21 +606,25 @@ __global__ void __launch_bounds__(128, ppt_min_blocks(M)) ppt_kernel(LaunchArgs 
     const int YS = ppt_frame_stride(M, FPW);  // floats per staged frame
     const int W = blockDim.x >> 5;
     // shared memory: the P decoders' maps and inverse maps as in the device table, the
-    // information positions, then per warp its frames' LLRs and a selection scratch
+    // information positions, the staged frames' LLRs, then per warp its level-(m-1) columns, a
+    // selection scratch and its reduction slots
     const int rec_elems = a.P * 2 * NREC * kRec;
     uint16_t* s_rec = reinterpret_cast<uint16_t*>(smem);
     uint16_t* s_info = s_rec + rec_elems;
     const int tables = ((rec_elems * 2 + K * 2) + 15) / 16 * 16;
-    const int warp_bytes = (D::PEND_FLOATS + FPW * YS) * 4 + 32;
+    float* s_y = reinterpret_cast<float*>(smem + tables);
+    const int ybytes = ((FPW * YS * 4) + 15) / 16 * 16;
+    const int warp_bytes = D::PEND_FLOATS * 4 + 32 + kPptSlotWords * 4;
     for (int i = threadIdx.x; i < rec_elems; i += blockDim.x) s_rec[i] = a.recs[i];
     for (int i = threadIdx.x; i < K; i += blockDim.x) s_info[i] = a.info[i];
-    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float* s_pend = reinterpret_cast<float*>(smem + tables + warp * warp_bytes);
-    float* s_y = s_pend + D::PEND_FLOATS;
-    uint8_t* s_sel = smem + tables + warp * warp_bytes + (D::PEND_FLOATS + FPW * YS) * 4;
+    uint8_t* wbase = smem + tables + ybytes;
+    float* s_pend = reinterpret_cast<float*>(wbase + warp * warp_bytes);
+    uint8_t* s_sel = wbase + warp * warp_bytes + D::PEND_FLOATS * 4;
+    auto slots = [&](int w) { return reinterpret_cast<uint32_t*>(wbase + w * warp_bytes + D::PEND_FLOATS * 4 + 32); };
     const int grp = lane / FW, j = lane % FW, gbase = grp * FW;
-    const int DPB = FW / DL;  // decoders per batch
+    const int DPB = FW / DL;                // decoders per batch
+    const int NB = (a.P + DPB - 1) / DPB;  // batches per frame
     const int ds = j / DL;
     typename D::Ctx c;
     c.y = s_y + grp * YS;
@@ -627,15 +637,15 @@ __global__ void __launch_bounds__(128, ppt_min_blocks(M)) ppt_kernel(LaunchArgs 
     const unsigned gmask = FW == 32 ? 0xffffffffu : ((1u << FW) - 1u);
     const size_t eb = a.dtype == IN_F32 ? 4 : (a.dtype == IN_I8 ? 1 : 2);
     const int64_t nblk = (a.n_frames + FPW - 1) / FPW;
-    for (int64_t fb = (int64_t)blockIdx.x * W + warp; fb < nblk; fb += (int64_t)gridDim.x * W) {
+    for (int64_t fb = blockIdx.x; fb < nblk; fb += gridDim.x) {
         const int64_t f0 = fb * FPW;
+        __syncthreads();  // the previous frames' LLRs and slots are no longer read
         // the FPW frames' LLRs (contiguous), 16 bytes per load, widened to float
         {
             const int chunks = (int)(FPW * N * eb / 16);
             const int per = (int)(16 / eb);  // values per chunk
             const uint4* src = reinterpret_cast<const uint4*>(static_cast<const uint8_t*>(a.llr) + f0 * N * eb);
-            __syncwarp();
-            for (int i = lane; i < chunks; i += 32) {
+            for (int i = threadIdx.x; i < chunks; i += blockDim.x) {
                 if (f0 + (int64_t)(i * per) / N >= a.n_frames) continue;
                 const uint4 q = src[i];
                 const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
@@ -667,16 +677,19 @@ __global__ void __launch_bounds__(128, ppt_min_blocks(M)) ppt_kernel(LaunchArgs 
                     dst[1] = make_float4(v8[4], v8[5], v8[6], v8[7]);
                 }
             }
-            __syncwarp();
         }
+        __syncthreads();
         const int64_t f = f0 + grp;
+        // this warp's best decoder over its batches (batches in increasing order: strict <
+        // keeps the earliest of equal metrics)
         unsigned best_key = 0xffffffffu;
-        int best_d = 0;
+        int best_d = 1 << 30;
         float best_pm = 0.f;
         uint32_t cw[NW];
 #pragma unroll
         for (int w = 0; w < NW; w++) cw[w] = 0;
-        for (int b0 = 0; b0 < a.P; b0 += DPB) {
+        for (int bt = warp; bt < NB; bt += W) {
+            const int b0 = bt * DPB;
             const int d = b0 + ds;
             const bool dvalid = d < a.P;
             const int dd = dvalid ? d : a.P - 1;
@@ -728,13 +741,43 @@ __global__ void __launch_bounds__(128, ppt_min_blocks(M)) ppt_kernel(LaunchArgs 
                     nw[w] |= ((__ballot_sync(kFull, b) >> gbase) & gmask) << o;
                 }
             }
-            if (bk < best_key || b0 == 0) {  // strict: earlier decoders win ties
+            if (bk < best_key || bt == warp) {  // strict: earlier decoders win ties
 #pragma unroll
                 for (int w = 0; w < NW; w++) cw[w] = nw[w];
                 best_key = bk;
                 best_d = dw;
                 best_pm = wpm == wpm ? wpm : __int_as_float(0x7f800000);
             }
+        }
+        // Algorithm 5 across the warps: the smallest (metric key, decoder) per frame
+        if (W > 1) {
+            uint32_t* sl = slots(warp) + grp * (3 + NW);
+            if (j == 0) {
+                sl[0] = best_key;
+                sl[1] = (uint32_t)best_d;
+                sl[2] = __float_as_uint(best_pm);
+            }
+            if (j < NW) sl[3 + j] = pick_word(cw, j);
+            __syncthreads();
+            if (warp != 0) continue;  // warp 0 writes the CTA's frames
+            int bw = 0;
+            unsigned bkey = 0xffffffffu;
+            int bdec = 1 << 30;
+            for (int w2 = 0; w2 < W; w2++) {
+                const uint32_t* o = slots(w2) + grp * (3 + NW);
+                const unsigned ok = o[0];
+                const int od = (int)o[1];
+                if (ok < bkey || (ok == bkey && od < bdec)) {
+                    bkey = ok;
+                    bdec = od;
+                    bw = w2;
+                }
+            }
+            const uint32_t* o = slots(bw) + grp * (3 + NW);
+            best_d = (int)o[1];
+            best_pm = __uint_as_float(o[2]);
+#pragma unroll
+            for (int w = 0; w < NW; w++) cw[w] = o[3 + w];
         }
         // outputs: codeword, metric, winner, and u = x G^{(x)m} at the information positions
         const bool fvalid = f < a.n_frames;

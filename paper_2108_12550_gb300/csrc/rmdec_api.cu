@@ -160,6 +160,11 @@ struct rmdec_ctx {
     uint16_t* d_recs = nullptr;
     uint16_t* d_info = nullptr;
     rmdec_host::KernelEntry kern;
+    // RMDEC_KERNEL_AUTO: the path-per-thread kernel, used for launches of at least
+    // kern_path.min_frames frames (fn null: none), and its launch shape
+    rmdec_host::KernelEntry kern_path;
+    int path_warps = 1, path_blocks_per_sm = 0;
+    size_t path_smem = 0;
     int warps = 4;
     int req_warps = 0, req_ctas = 0;  // requested launch shape (0 = default)
     bool shape_dirty = true;
@@ -214,8 +219,7 @@ bool lookup_kernel(rmdec_ctx* h, rmdec_host::KernelEntry* e) {
     if (h->algo == 1) return lookup_autssc(h->m, h->r, e);
     if (h->algo == 2) return lookup_mlroot(h->m, h->r, e);
     if (h->hadamard == RMDEC_HADAMARD_TENSOR) return lookup_pfht_tc(h->m, h->r, h->L, e);
-    if (h->kernel != RMDEC_KERNEL_WARP && lookup_pfht_ppt(h->m, h->r, h->L, h->P, e)) return true;
-    if (h->kernel == RMDEC_KERNEL_PATH) return false;
+    if (h->kernel == RMDEC_KERNEL_PATH) return lookup_pfht_ppt(h->m, h->r, h->L, h->P, e);
     if (h->L == 32) {
         if (h->m == 9) return lookup_pfht_l32_m9(h->r, e);
         if (h->m == 8) return lookup_pfht_l32_m8(h->r, e);
@@ -232,6 +236,13 @@ bool lookup_kernel(rmdec_ctx* h, rmdec_host::KernelEntry* e) {
         case 10: return lookup_pfht_m10(h->r, h->L, e);
     }
     return false;
+}
+
+// RMDEC_KERNEL_AUTO: the path-per-thread kernel that takes the larger launches, if any.
+bool lookup_path_alternative(rmdec_ctx* h, rmdec_host::KernelEntry* e) {
+    *e = rmdec_host::KernelEntry();
+    if (h->algo != 0 || h->kernel != RMDEC_KERNEL_AUTO || h->hadamard != RMDEC_HADAMARD_SHUFFLE) return false;
+    return rmdec_host::lookup_pfht_ppt(h->m, h->r, h->L, h->P, e);
 }
 
 // Device records: p-FHT-FSCL: per decoder, level 0 holds the 2L root candidates composed with
@@ -267,6 +278,7 @@ rmdec_status ensure_device(rmdec_ctx* h) {
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return h->fail(RMDEC_EDEVICE, "no CUDA device: %s", cudaGetErrorString(e));
     if (!lookup_kernel(h, &h->kern)) return h->fail(RMDEC_EINVAL, "no kernel for m=%d r=%d L=%d", h->m, h->r, h->L);
+    lookup_path_alternative(h, &h->kern_path);
     if ((e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return h->cuda_fail(e, "cudaDeviceGetAttribute");
     std::vector<uint16_t> recs = device_records(h);
@@ -305,7 +317,8 @@ int max_warps_per_cta(const rmdec_ctx* h, const rmdec_host::KernelEntry& k) {
 }
 
 // Default warps per CTA, given the resident CTAs occ_for(W) of each width W <= wmax.
-// Kernels whose CTA decodes one frame with all its warps: four warps (else three, else two)
+// Path-per-thread kernels: one.
+// Warp-per-decoder kernels, whose CTA decodes one frame with all its warps: four warps (else three, else two)
 // when that width splits the P decoders evenly and keeps at least two thirds of the most
 // resident warps. Its warps run their decoders in lockstep (a block barrier at every leaf),
 // which keeps them on the same code; the trees of the longer codes exceed the instruction
@@ -314,12 +327,17 @@ int max_warps_per_cta(const rmdec_ctx* h, const rmdec_host::KernelEntry& k) {
 // same shape), RM(3,9) P=20 2.90 (2.73 at 2 x 10), RM(3,9) P=8 7.11 (6.65), RM(3,8) P=8 12.86
 // (12.15 at 1 x 20), RM(2,10) P=8 5.93 (5.35 at 2 x 5), RM(3,10) P=8 2.79 (2.28 at 6 x 2); no
 // other width was more than 6% faster on any of 15 codes and list sizes.
-// Otherwise, and for the kernels whose warps decode frames of their own: the most resident
+// Otherwise, and for the kernels that decode one frame per warp: the most resident
 // warps per SM; among equals, widths that split the P decoders evenly, then at least two
 // decoders per warp and two or more CTAs per SM (a lone decoder per warp, or a lone CTA,
 // leaves the SM idle at every frame boundary), then the narrowest CTA.
 template <typename Occ>
 int default_warps(const rmdec_ctx* h, const rmdec_host::KernelEntry& k, int wmax, Occ occ_for) {
+    // path-per-thread kernels: one warp per CTA (measured: splitting a frame's decoder batches
+    // over the warps of a CTA shortens a lone frame's wait but lowers the throughput of large
+    // launches, which are the ones these kernels take; RM(2,8) P=20 L=4, 65,536 frames: 5.30 ms
+    // at one warp, 8.52 ms at four)
+    if (k.frames_per_warp) return 1;
     const bool bpf = block_per_frame(h, k);
     int most = 0;
     for (int c = 1; c <= wmax; c++) most = std::max(most, occ_for(c) * c);
@@ -378,6 +396,23 @@ rmdec_status configure_shape(rmdec_ctx* h) {
     const int occ = occ_for(W);
     if (occ < 1) return h->fail(RMDEC_EINVAL, "kernel cannot be resident (smem %zu)", h->smem);
     h->blocks_per_sm = h->req_ctas ? std::min(h->req_ctas, occ) : occ;
+    if (h->kern_path.fn) {
+        // the path-per-thread alternative: the requested width (at most its four warps) or one
+        const rmdec_host::KernelEntry& k = h->kern_path;
+        if ((e = cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)) != cudaSuccess)
+            return h->cuda_fail(e, "cudaFuncSetAttribute");
+        const int pw = h->req_warps ? std::max(1, std::min(max_warps_per_cta(h, k), h->req_warps)) : 1;
+        const size_t ps = (size_t)k.fixed_bytes(h->P, h->k, pw) + 16 + (size_t)pw * k.warp_bytes;
+        int po = 0;
+        if (ps > (size_t)max_optin || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&po, k.fn, 32 * pw, ps) != cudaSuccess) po = 0;
+        if (po < 1) {
+            h->kern_path = rmdec_host::KernelEntry();  // not resident: the warp kernel takes every launch
+        } else {
+            h->path_warps = pw;
+            h->path_smem = ps;
+            h->path_blocks_per_sm = h->req_ctas ? std::min(h->req_ctas, po) : po;
+        }
+    }
     h->shape_dirty = false;
     return RMDEC_OK;
 }
@@ -391,6 +426,31 @@ rmdec_status launch(rmdec_ctx* h, const void* llr, int64_t n_frames, uint32_t* b
     rmdec_status st = ensure_device(h);
     if (st == RMDEC_OK) st = configure_shape(h);
     if (st != RMDEC_OK) return st;
+    if (h->kern_path.fn && n_frames >= h->kern_path.min_frames) {
+        // large launches of short codes: the path-per-thread kernel (see lookup_pfht_ppt)
+        rmdec_dev::LaunchArgs a;
+        a.llr = llr;
+        a.dtype = (int)h->dtype;
+        a.qclamp = (float)((1 << (24 - h->m)) - 1);
+        a.n_frames = n_frames;
+        a.P = h->P;
+        a.recs = h->d_recs;
+        a.info = h->d_info;
+        a.K = h->k;
+        a.info_out = bits;
+        a.cw_out = cw;
+        a.pm_out = pm;
+        a.best_out = best;
+        a.single_start = h->single_start ? 1 : 0;
+        const int64_t want = (n_frames + h->kern_path.frames_per_warp - 1) / h->kern_path.frames_per_warp;
+        const unsigned grid = (unsigned)std::min<int64_t>(want, (int64_t)h->sm_count * h->path_blocks_per_sm);
+        void* args[] = {&a};
+        nvtxRangePushA("rmdec_decode pfht path-per-thread");
+        cudaError_t e = cudaLaunchKernel(h->kern_path.fn, dim3(grid), dim3(32 * h->path_warps), args, h->path_smem, stream);
+        nvtxRangePop();
+        if (e != cudaSuccess) return h->cuda_fail(e, "kernel launch");
+        return RMDEC_OK;
+    }
     // Launches of a few waves: the last, partial wave costs a whole frame's worth of decoder
     // rounds (P / W decoders one after another per warp), so such launches take the shape
     // that minimises waves x rounds (ties: the default shape). Larger launches keep the
@@ -431,9 +491,10 @@ rmdec_status launch(rmdec_ctx* h, const void* llr, int64_t n_frames, uint32_t* b
     a.single_start = h->single_start ? 1 : 0;
     const int64_t cap = (int64_t)h->sm_count * per_sm;
     // p-FHT-FSCL and Aut-SSC CTAs take one frame at a time; the first-order/parity-check root
-    // kernel decodes one frame per warp, the path-per-thread kernel frames_per_warp per warp
-    const int64_t fpw = h->algo == 2 ? 1 : h->kern.frames_per_warp;
-    const int64_t want = fpw ? (n_frames + W * fpw - 1) / (W * fpw) : n_frames;
+    // kernel decodes one frame per warp, the path-per-thread kernel frames_per_warp per CTA
+    int64_t want = n_frames;
+    if (h->algo == 2) want = (n_frames + W - 1) / W;
+    else if (h->kern.frames_per_warp) want = (n_frames + h->kern.frames_per_warp - 1) / h->kern.frames_per_warp;
     const unsigned grid = (unsigned)std::min<int64_t>(want, cap);
     void* args[] = {&a};
     nvtxRangePushA(h->algo == 1 ? "rmdec_decode aut-ssc" : "rmdec_decode pfht");
@@ -529,7 +590,7 @@ rmdec_status member_info(rmdec_ctx* h, bool prepare, MemberInfo* out) {
     out->nrec = h->dirty ? 0 : h->kern.nrec;
     out->device = h->dirty ? -1 : h->device;
     out->wave = (h->dirty || h->shape_dirty) ? 0 : (int64_t)h->sm_count * h->blocks_per_sm;
-    out->path_kernel = !h->dirty && h->kern.frames_per_warp != 0;
+    out->path_min_frames = h->dirty ? -1 : (h->kern.frames_per_warp ? 0 : (h->kern_path.fn ? h->kern_path.min_frames : -1));
     return RMDEC_OK;
 }
 }  // namespace rmdec_host
@@ -1033,6 +1094,10 @@ extern "C" rmdec_status rmdec_decode_noalloc(rmdec_t h, const void* llr_dev, int
     if (dev < 0 || dev >= kNoAllocMaxDevices) return h->fail(RMDEC_EDEVICE, "device %d beyond the supported %d", dev, kNoAllocMaxDevices);
     rmdec_host::KernelEntry kern;
     if (!lookup_kernel(h, &kern)) return h->fail(RMDEC_EINVAL, "no kernel for m=%d r=%d L=%d", h->m, h->r, h->L);
+    {
+        rmdec_host::KernelEntry kp;  // the same kernel choice as rmdec_decode's
+        if (lookup_path_alternative(h, &kp) && n_frames >= kp.min_frames) kern = kp;
+    }
     int sms = 0, max_optin = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
         (e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)

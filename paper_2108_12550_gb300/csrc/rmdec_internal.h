@@ -25,7 +25,9 @@ struct KernelEntry {
     int warp_bytes = 0;        // shared memory per warp
     int nrec = 0;              // permutation maps per decoder held in block shared memory
     int (*fixed_bytes)(int P, int K, int W) = nullptr;
-    int frames_per_warp = 0;   // path-per-thread kernels: frames a warp decodes at once (else 0)
+    int frames_per_warp = 0;   // path-per-thread kernels: frames a CTA decodes at once (else 0)
+    int batches = 0;           // path-per-thread kernels: decoder batches per frame
+    int64_t min_frames = 0;    // path-per-thread kernels: smallest launch they take by default
 };
 
 // p-FHT-FSCL kernels: one lookup per code length m (instantiated in inst_m<m>.cu).
@@ -70,7 +72,8 @@ struct MemberInfo {
     int nrec = 0;  // permutation maps per decoder held in block shared memory
     int device = -1;
     int64_t wave = 0;  // CTAs of the handle's own launch resident at once (valid after prepare)
-    bool path_kernel = false;  // decodes with the path-per-thread kernel (valid after prepare)
+    int64_t path_min_frames = -1;  // launches of at least this many frames use the
+                                   // path-per-thread kernel (-1: none; valid after prepare)
 };
 // Fills *out from the handle; with prepare = true first uploads the handle's tables to the
 // current device and fixes its own launch shape (errors are recorded on the handle, see

@@ -96,6 +96,7 @@ def test_tuning_shapes_and_tiny_batches():
     fr = I.make_frames(m, r, 700, 2.0, seed=12)
     q = I.quantize_i8(fr["llr"])
     dec = pkg.Decoder(m, r, P, L, dtype="i8", perm_seed=4)
+    dec.set_kernel("path")
     ref = _run(dec, q)
     for w in (1, 2, 3, 4):
         dec.set_tuning(w, 0)
@@ -107,11 +108,26 @@ def test_tuning_shapes_and_tiny_batches():
         got = _run(dec, q[:n])
         assert all(np.array_equal(a[:n], b) for a, b in zip(ref, got)), n
     small = pkg.Decoder(5, 2, 1, 1, dtype="i8", perm_seed=2)  # 32 frames per warp
+    small.set_kernel("path")
     fr5 = I.make_frames(5, 2, 77, 2.0, seed=3)
     q5 = I.quantize_i8(fr5["llr"])
     a = _run(small, q5)
     small.set_kernel("warp")
     assert all(np.array_equal(x, y) for x, y in zip(a, _run(small, q5)))
+
+
+def test_auto_takes_each_kernel_by_launch_size():
+    # 'auto' gives small launches to the warp kernel and large ones to the path kernel; on
+    # integer LLRs both decode identically, so the results of one batch decoded whole and in
+    # small pieces agree
+    m, r, P, L = 7, 2, 8, 4
+    fr = I.make_frames(m, r, 5000, 2.0, seed=14)
+    q = I.quantize_i8(fr["llr"])
+    dec = pkg.Decoder(m, r, P, L, dtype="i8", perm_seed=4)
+    whole = _run(dec, q)  # >= 2,048 frames: path-per-thread kernel
+    parts = [_run(dec, q[i:i + 500]) for i in range(0, 5000, 500)]  # warp kernel
+    for k in range(4):
+        assert np.array_equal(whole[k], np.concatenate([p[k] for p in parts])), k
 
 
 def test_kernel_choice_is_validated():
