@@ -116,6 +116,23 @@ def test_tuning_shapes_and_tiny_batches():
     assert all(np.array_equal(x, y) for x, y in zip(a, _run(small, q5)))
 
 
+def test_decoder_batches_split_over_the_warps_of_a_cta():
+    # RM(2,8) P=20 L=4: five batches of four decoders per frame; one to four warps per CTA
+    # split them, and the warps' best decoders meet in shared memory
+    m, r, P, L = 8, 2, 20, 4
+    fr = I.make_frames(m, r, 203, 2.0, seed=15)
+    q = I.quantize_i8(fr["llr"])
+    perms = I.perm_table(m, r, P, L, seed=16)
+    ref = O.decode(m, r, P, L, perms, q.astype(np.int64), integer=True)
+    dec = pkg.Decoder(m, r, P, L, dtype="i8", perms=perms)
+    dec.set_kernel("path")
+    for w in (1, 2, 3, 4):
+        dec.set_tuning(w, 0)
+        bits, cw, pm, best = _run(dec, q)
+        assert np.array_equal(pkg.unpack_bits(cw, dec.n), ref["cw"]), w
+        assert np.array_equal(best, ref["best"]) and np.array_equal(pm.astype(np.int64), ref["pm"]), w
+
+
 def test_auto_takes_each_kernel_by_launch_size():
     # 'auto' gives small launches to the warp kernel and large ones to the path kernel; on
     # integer LLRs both decode identically, so the results of one batch decoded whole and in
