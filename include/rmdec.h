@@ -112,13 +112,14 @@ typedef enum {
 rmdec_status rmdec_set_hadamard(rmdec_t h, rmdec_hadamard mode);
 
 /* Which kernel runs a p-FHT-FSCL decode (Algorithms 2-5; the same method either way).
- * AUTO (default): WARP, and PATH for launches of at least 512 (m <= 5), 2,048 (m = 6, 7) or
- *   8,192 (m = 8) frames where it exists (measured crossovers: the warp kernel answers small
- *   launches sooner, the path kernel has the higher throughput).
+ * AUTO (default): WARP, and PATH for launches of at least 512 (RM(2, m <= 5)), 2,048 (RM(2, 6),
+ *   RM(2, 7), RM(3, m)) or 8,192 (RM(2, 8)) frames where it exists (measured crossovers: the
+ *   warp kernel answers small launches sooner, the path kernel has the higher throughput).
  * WARP: one warp per decoder, the L paths spread over its lanes and the tree's LLR buffers in
  *   shared memory; every supported code.
  * PATH: one thread per list path (two for m = 8), the tree's LLRs in registers, the decoders
- *   of a frame in one lane group; RM(2, m) with 4 <= m <= 8 and L in {1, 2, 4, 8}, FP32 butterflies
+ *   of a frame in one lane group; RM(2, m) with 4 <= m <= 8 and RM(3, m) with 5 <= m <= 7, L in
+ *   {1, 2, 4, 8}, FP32 butterflies
  *   (RMDEC_EINVAL otherwise). Integer inputs decode identically under both; FP32 inputs may
  *   differ where two FHTL candidates of one path round to the same FP32 metric (WARP then
  *   prefers the smaller index, PATH the larger |c_k|). Segments of a grouped launch that

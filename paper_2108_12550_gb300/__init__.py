@@ -156,8 +156,8 @@ class Decoder:
 
     def set_kernel(self, kernel):
         """'auto' (default: 'warp', and 'path' for large launches where it exists), 'warp' (one
-        warp per decoder) or 'path' (one thread per list path, RM(2, m) with 4 <= m <= 8 and
-        L <= 8)."""
+        warp per decoder) or 'path' (one thread per list path, RM(2, m) with 4 <= m <= 8 or
+        RM(3, m) with 5 <= m <= 7, and L <= 8)."""
         self._check(self._lib.rmdec_set_kernel(self._h, {"auto": 0, "warp": 1, "path": 2}[kernel]))
         self.kernel = kernel
 

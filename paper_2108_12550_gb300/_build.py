@@ -18,9 +18,9 @@ NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-
 
 # slowest units first, so that they start first in the parallel build
 UNITS = (["group_l8.cu", "inst_m10.cu", "inst_r4_m9.cu", "inst_l32_m9.cu", "inst_r4_m6_8.cu", "inst_tc.cu",
-          "inst_l32_m8.cu", "inst_l32_m4_7.cu", "group_l4.cu", "group_l2.cu", "group_l1.cu", "inst_ppt.cu"] + [f"inst_m{m}.cu" for m in range(9, 3, -1)]
+          "inst_l32_m8.cu", "inst_l32_m4_7.cu", "group_l4.cu", "group_l2.cu", "group_l1.cu", "inst_ppt.cu", "inst_ppt3.cu"] + [f"inst_m{m}.cu" for m in range(9, 3, -1)]
          + ["rmdec_api.cu", "autssc.cu", "mlroot.cu", "serve.cu", "group.cu"])
-HEADERS = ["pfht_kernel.cuh", "ppt_kernel.cuh", "group_kernel.cuh", "rmdec_internal.h"]
+HEADERS = ["pfht_kernel.cuh", "ppt_kernel.cuh", "ppt_entry.cuh", "group_kernel.cuh", "rmdec_internal.h"]
 
 
 def _nvcc() -> str:

@@ -1,52 +1,18 @@
-// Kernel instances of the path-per-thread decoder for RM(2, m), 4 <= m <= 8 (ppt_kernel.cuh).
-#include "ppt_kernel.cuh"
-#include "rmdec_internal.h"
+// Kernel instances of the path-per-thread decoder for RM(2, m), 4 <= m <= 8 (ppt_kernel.cuh);
+// RM(3, m) in inst_ppt3.cu.
+#include "ppt_entry.cuh"
 
 namespace rmdec_host {
 
-namespace {
-template <int M, int L>
-bool ppt_entry(int P, KernelEntry* e) {
-    using D = rmdec_dev::Ppt<M, L>;
-    const int fw = rmdec_dev::ppt_frame_lanes(M, L, P);
-    e->fn = reinterpret_cast<const void*>(&rmdec_dev::ppt_kernel<M, L>);
-    e->frames_per_warp = 32 / fw;  // frames a CTA stages at a time
-    const int per_batch = fw / D::DL;
-    e->batches = (P + per_batch - 1) / per_batch;
-    // Smallest launch this kernel takes by default (the warp-per-decoder kernel takes smaller
-    // ones): where it overtook that kernel, measured with CUDA events over 64..65,536 frames
-    // (FP32, L = 4 unless stated): RM(2,5) P=4 L=2 from 512 frames, RM(2,6) P=8 and RM(2,7) P=8
-    // INT8 / P=20 from 2,048, RM(2,8) P=8 / P=20 from 8,192.
-    e->min_frames = M <= 5 ? 512 : (M <= 7 ? 2048 : 8192);
-    e->warp_bytes = D::PEND_FLOATS * 4 + 32 + rmdec_dev::kPptSlotWords * 4;
-    e->nrec = 0;  // the maps sit in the fixed part
-    e->fixed_bytes = [](int P2, int K, int) {
-        const int fpw = 32 / rmdec_dev::ppt_frame_lanes(M, L, P2);
-        const int tables = ((P2 * 2 * rmdec_dev::Ppt<M, L>::NREC * rmdec_dev::kRec * 2 + K * 2) + 15) / 16 * 16;
-        return tables + ((fpw * rmdec_dev::ppt_frame_stride(M, fpw) * 4) + 15) / 16 * 16;
-    };
-    return true;
-}
-template <int M>
-bool ppt_case(int L, int P, KernelEntry* e) {
-    switch (L) {
-        case 1: return ppt_entry<M, 1>(P, e);
-        case 2: return ppt_entry<M, 2>(P, e);
-        case 4: return ppt_entry<M, 4>(P, e);
-        case 8: return ppt_entry<M, 8>(P, e);
-    }
-    return false;
-}
-}  // namespace
-
 bool lookup_pfht_ppt(int m, int r, int L, int P, KernelEntry* e) {
+    if (r == 3) return lookup_pfht_ppt3(m, L, P, e);
     if (r != 2) return false;
     switch (m) {
-        case 4: return ppt_case<4>(L, P, e);
-        case 5: return ppt_case<5>(L, P, e);
-        case 6: return ppt_case<6>(L, P, e);
-        case 7: return ppt_case<7>(L, P, e);
-        case 8: return ppt_case<8>(L, P, e);
+        case 4: return ppt_case<4, 2>(L, P, e);
+        case 5: return ppt_case<5, 2>(L, P, e);
+        case 6: return ppt_case<6, 2>(L, P, e);
+        case 7: return ppt_case<7, 2>(L, P, e);
+        case 8: return ppt_case<8, 2>(L, P, e);
     }
     return false;
 }

@@ -1,10 +1,10 @@
-// p-FHT-FSCL-L-M for the short codes RM(2, m), 4 <= m <= 8, with one thread per list path
-// (two threads per path for m = 8).
+// p-FHT-FSCL-L-M for the short codes RM(2, m), 4 <= m <= 8, and RM(3, m), 5 <= m <= 7, with
+// one thread per list path (two threads per path for m = 8).
 //
-// Method: Doan, Hashemi, Gross, arXiv 2108.12550 — Algorithm 2 (the root is the one permuted
-// node of an RM(2, m) tree: 2L candidate permutations ranked by the reliability metric LM),
-// Algorithms 3-4 with Eq. (8) (FHTL nodes RM(1, s)), Eqs. (2)-(6) (the SPCL node RM(2, 3)) and
-// Algorithm 5 (the best of P decoders).
+// Method: Doan, Hashemi, Gross, arXiv 2108.12550 — Algorithm 2 (the permuted nodes: the root,
+// and for RM(3, m) also its left child RM(2, m-1); 2L candidate permutations each, ranked by the
+// reliability metric LM), Algorithms 3-4 with Eq. (8) (FHTL nodes RM(1, s)), Eqs. (2)-(6) (the
+// SPCL nodes RM(2, 3) and RM(3, 4)) and Algorithm 5 (the best of P decoders).
 //
 // Execution model. The L paths of one decoder are G L consecutive lanes of a warp (G = 1 lane
 // per path, or G = 2 for m = 8: lane g of a path holds its positions i = G e + g); a lane keeps
@@ -62,6 +62,28 @@ __host__ __device__ constexpr int ctz7(int n) {
     return (n & 1) ? 0 : (n & 2) ? 1 : (n & 4) ? 2 : (n & 8) ? 3 : (n & 16) ? 4 : (n & 32) ? 5 : 6;
 }
 
+// Batcher's odd-even merge sort network on NS = 2^k inputs (Knuth's formulation), as a
+// compile-time list of comparators (19 for NS = 8, 63 for NS = 16), so that the sorting code
+// unrolls into straight-line compare-exchanges on registers.
+template <int NS>
+struct OddEvenMergeNet {
+    static constexpr int kMax = 64;
+    int n = 0;
+    int lo[kMax] = {};
+    int hi[kMax] = {};
+    constexpr OddEvenMergeNet() {
+        for (int pp = 1; pp < NS; pp <<= 1)
+            for (int k = pp; k >= 1; k >>= 1)
+                for (int j = k % pp; j + k < NS; j += 2 * k)
+                    for (int i = 0; i < k; i++)
+                        if (i + j + k < NS && (i + j) / (2 * pp) == (i + j + k) / (2 * pp)) {
+                            lo[n] = i + j;
+                            hi[n] = i + j + k;
+                            n++;
+                        }
+    }
+};
+
 // Word `idx` (< NW <= 8) of a register array, by a multiplexer on the index bits (an equality
 // chain would be turned into a local-memory array by the compiler).
 template <int NW>
@@ -82,26 +104,32 @@ __device__ __forceinline__ uint32_t pick_word(const uint32_t (&x)[NW], int idx) 
     }
 }
 
-template <int M, int L>
+template <int M, int R, int L>
 struct Ppt {
     static constexpr int G = ppt_lanes_per_path(M);  // lanes per path
     static constexpr int DL = G * L;                  // lanes per decoder
     static constexpr int N = 1 << M;
     static constexpr int H = N / 2;
     static constexpr int NW = (N + 31) / 32;
-    static constexpr int NREC = 2 * L;  // root candidates per decoder (one permuted level)
-    // The LLRs of level m-1 wait in shared memory (a column per lane) while the leaf RM(1, m-2)
-    // is decoded, instead of in registers: the register peak, and so the resident warps, then
-    // follow the largest leaf alone.
-    static constexpr bool PEND_SMEM = M >= 6;
-    static constexpr int PEND_FLOATS = PEND_SMEM ? (H / G) * 32 : 0;  // per warp
+    static constexpr int NREC = 2 * L * (R - 1);  // candidate maps per decoder (R - 1 permuted levels)
+    // Shared-memory columns (value e of lane t at word 32 e + t): RM(2, m) keeps the LLRs of
+    // level m-1 there (m >= 6) while the leaf RM(1, m-2) is decoded, instead of in registers,
+    // so that the register peak, and with it the resident warps, follows the largest leaf alone.
+    // RM(3, m) keeps there the permuted node's LLRs (the candidates gather from them) and the
+    // pending LLRs of its RM(3, s) nodes of levels m-1 and m-2 while their left subtrees run.
+    static constexpr bool PEND_SMEM = R == 3 || M >= 6;
+    static constexpr int COL1 = (R == 3 && M - 2 >= 5) ? (1 << (M - 2)) : 0;  // level m-2 column
+    static constexpr int PEND_FLOATS = PEND_SMEM ? (H / G + COL1) * 32 : 0;   // per warp
     static_assert(M >= 4 && M <= 8, "short codes");
+    static_assert(R == 2 || (R == 3 && M >= 5 && M <= 7 && G == 1), "RM(2, m); RM(3, m) for m <= 7");
     static_assert(L == 1 || L == 2 || L == 4 || L == 8, "list size");
     static_assert(DL <= 32, "a decoder within a warp");
 
     struct Ctx {
         const float* y;         // the frame's LLRs (shared memory)
-        const uint16_t* rec;    // the decoder's 2L composed root records (shared memory)
+        const uint16_t* rec;    // the decoder's maps: 2L composed root records, then (R = 3) the
+                                // 2L records of the permuted node RM(2, m-1) (shared memory)
+        const uint16_t* rinv;   // their inverse maps, in the same order (shared memory)
         uint8_t* sel;           // the warp's 32-byte selection scratch
         float* pend;            // the warp's level-(m-1) LLRs: value e of lane t at [32 e + t]
         int dbase;              // lane of the decoder's path 0
@@ -112,6 +140,8 @@ struct Ppt {
     struct Path {
         float pm;
         int rootc;         // root candidate (composed permutation) the path descends from
+        int selc;          // R = 3: the candidate chosen at the permuted node RM(2, m-1)
+        int own[2];        // R = 3: lanes whose columns hold the ancestors' pending LLRs
         uint32_t x[NW];    // decided bits of the permuted word, span layout of the tree
     };
 
@@ -151,6 +181,11 @@ struct Ppt {
     __device__ __forceinline__ static void list_step(const Ctx& c, Path& p, int par, float (&pend)[PA]) {
         const int src = lane_of(c, par);
         p.rootc = __shfl_sync(kFull, p.rootc, src);
+        if constexpr (R == 3) {
+            p.selc = __shfl_sync(kFull, p.selc, src);
+            p.own[0] = __shfl_sync(kFull, p.own[0], src);
+            p.own[1] = __shfl_sync(kFull, p.own[1], src);
+        }
 #pragma unroll
         for (int i = 0; i < PC; i++) pend[i] = __shfl_sync(kFull, pend[i], src);
 #pragma unroll
@@ -327,9 +362,8 @@ struct Ppt {
     // RM(2, 3) node (Eqs. (2)-(6)): parity, PM += p |alpha_lrb|, then tau = min(L, 7) list
     // splits on the next least reliable positions (flip cost |alpha_i| + (1-2p)|alpha_lrb|, each
     // a 2L -> L selection by (PM, 2 path + flip)); the least reliable bit restores even parity.
-    template <int OFF>
-    __device__ __forceinline__ static void spc_leaf(const Ctx& c, Path& p, float (&as)[8 / G]) {
-        constexpr int NS = 8;
+    template <int OFF, int NS>
+    __device__ __forceinline__ static void spc_leaf(const Ctx& c, Path& p, float (&as)[NS / G]) {
         constexpr int TAU = cmin(L, NS - 1);
         // the node's 8 LLRs in every lane of the path (both lanes of a path then hold the same
         // state and take the same decisions; shuffles read a path's lane g = 0)
@@ -362,12 +396,10 @@ struct Ppt {
             sv[j] = sw ? tv : sv[j];
             sp[j] = sw ? tp : sp[j];
         };
-        cx(0, 1); cx(2, 3); cx(4, 5); cx(6, 7);
-        cx(0, 2); cx(1, 3); cx(4, 6); cx(5, 7);
-        cx(1, 2); cx(5, 6);
-        cx(0, 4); cx(1, 5); cx(2, 6); cx(3, 7);
-        cx(2, 4); cx(3, 5);
-        cx(1, 2); cx(3, 4); cx(5, 6);
+        constexpr OddEvenMergeNet<NS> net;
+        static_assert(net.n <= OddEvenMergeNet<NS>::kMax, "comparators");
+#pragma unroll
+        for (int t = 0; t < net.n; t++) cx(net.lo[t], net.hi[t]);
         const int o0 = sp[0];
         const float lrb = sv[0];
         float rel[TAU];
@@ -429,7 +461,8 @@ struct Ppt {
         const int so = c.dbase + G * orig;
         const unsigned hd_o = __shfl_sync(kFull, hd, so);
         const int lo0 = __shfl_sync(kFull, o0, so) & (NS - 1);
-        unsigned x = ((hd_o ^ flip) & 0xffu) & ~(1u << lo0);
+        constexpr unsigned span = (1u << NS) - 1u;
+        unsigned x = ((hd_o ^ flip) & span) & ~(1u << lo0);
         x |= (unsigned)(__popc(x) & 1) << lo0;  // Eq. (6)
         p.pm = pm;
         float none[1];
@@ -439,15 +472,15 @@ struct Ppt {
 
     // ------------------------------------------------------------- tree walk ---
     // RM(2, S) node off the root (not permuted), LLRs `a`, at span offset OFF
-    template <int S, int OFF>
+    template <int S, int OFF, bool COL = (R == 2 && PEND_SMEM && S == M - 1)>
     __device__ __forceinline__ static void node2(const Ctx& c, Path& p, float (&a)[(1 << S) / G]) {
         if constexpr (S == 3) {
-            spc_leaf<OFF>(c, p, a);
+            spc_leaf<OFF, 8>(c, p, a);
         } else {
             constexpr int HS = 1 << (S - 1);
             constexpr int VH = HS / G;  // this lane's share of a child's positions
             float ch[VH];
-            if constexpr (PEND_SMEM && S == M - 1) {
+            if constexpr (COL) {
                 // park the node's LLRs in this lane's column; the new path reads its parent's
                 const int lane = c.dbase + G * c.l + c.g;
                 __syncwarp();  // every lane has read the previous decoder's columns
@@ -469,6 +502,127 @@ struct Ppt {
                 for (int e = 0; e < VH; e++) ch[e] = g_fn(a[e], a[e + VH], bitg(p, OFF + G * e, c.g));
             }
             node2<S - 1, OFF + HS>(c, p, ch);
+            combine<OFF, HS>(p);
+        }
+    }
+
+    // RM(2, m-1), the left child of an RM(3, m) root: a permuted node (Algorithm 2). Candidate c'
+    // of path l (c' = l, l + L) permutes the path's LLRs, which every path parks in its lane's
+    // column: LM in the warp-per-decoder kernel's summation order, the L best candidates, then
+    // the new path's LLRs gathered from its source path's column through the candidate's map;
+    // after the subtree the span is un-permuted through the inverse map.
+    template <int S>
+    __device__ __forceinline__ static void node2p(const Ctx& c, Path& p, float (&a)[1 << S]) {
+        static_assert(R == 3 && G == 1 && S == M - 1, "the permuted child of an RM(3, m) root");
+        constexpr int NS = 1 << S;
+        constexpr int HALF = NS / 2;
+        const int lane = c.dbase + c.l;
+        __syncwarp();  // every lane has read the previous decoder's columns
+#pragma unroll
+        for (int e = 0; e < NS; e++) c.pend[32 * e + lane] = a[e];
+        __syncwarp();
+        const uint16_t* lrec = c.rec + 2 * L * kRec;  // this level's 2L records
+        const float* mine_col = c.pend + lane;
+        constexpr int V = HALF < 32 ? HALF : 32;
+        float lm[2];
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            const uint16_t* r = lrec + (c.l + q * L) * kRec;
+            const int am = r[S - 1];
+            const int hm = ~((1 << (31 - __clz(am))) - 1);
+            float acc[V];
+#pragma unroll
+            for (int lv = 0; lv < V; lv++) {
+                float sum = 0.f;
+#pragma unroll
+                for (int t = 0; t < (HALF + 31) / 32; t++) {
+                    const int jp = lv + 32 * t;
+                    const int j = jp + (jp & hm);
+                    sum += fminf(fabsf(mine_col[32 * j]), fabsf(mine_col[32 * (j ^ am)]));
+                }
+                acc[lv] = sum;
+            }
+#pragma unroll
+            for (int d = 16; d >= 1; d >>= 1)
+#pragma unroll
+                for (int lv = 0; lv < d; lv++)
+                    if (lv + d < V) acc[lv] += acc[lv + d];
+            lm[q] = acc[0];
+        }
+        const int cq = pick_by_rank(c, lm);
+        // the new path takes its source path's state, and its LLRs through pi_c: a'[i] = a_src[pi(i)]
+        const int src = c.dbase + (cq & (L - 1));
+        p.pm = __shfl_sync(kFull, p.pm, src);
+        p.rootc = __shfl_sync(kFull, p.rootc, src);
+        p.selc = cq;
+        {
+            const uint16_t* r = lrec + cq * kRec;
+            int pc[S];
+#pragma unroll
+            for (int t = 0; t < S; t++) pc[t] = r[t];
+            const float* scol = c.pend + src;
+            int sv = r[10];
+#pragma unroll
+            for (int n = 0; n < NS; n++) {
+                if (n) sv ^= pc[ctz7(n)];
+                a[n ^ (n >> 1)] = scol[32 * sv];
+            }
+        }
+        node2<S, 0, true>(c, p, a);
+        // undo pi on the span: x[j] = x'[pi^-1(j)], through the stored inverse map
+        {
+            const uint16_t* ri = c.rinv + (2 * L + p.selc) * kRec;
+            int ic[S];
+#pragma unroll
+            for (int t = 0; t < S; t++) ic[t] = ri[t];
+            constexpr int SW = (NS + 31) / 32;
+            uint32_t nx[SW];
+#pragma unroll
+            for (int w = 0; w < SW; w++) nx[w] = 0;
+            int tv = ri[10];
+#pragma unroll
+            for (int n = 0; n < NS; n++) {
+                if (n) tv ^= ic[ctz7(n)];
+                const int jj = n ^ (n >> 1);
+                const uint32_t word = (SW > 1 && (tv >> 5)) ? p.x[SW > 1 ? 1 : 0] : p.x[0];
+                nx[jj >> 5] |= ((word >> (tv & 31)) & 1u) << (jj & 31);
+            }
+            if constexpr (NS >= 32) {
+#pragma unroll
+                for (int w = 0; w < SW; w++) p.x[w] = nx[w];
+            } else {
+                constexpr uint32_t mask = (1u << NS) - 1u;
+                p.x[0] = (p.x[0] & ~mask) | nx[0];
+            }
+        }
+    }
+
+    // RM(3, S) node on the right spine of an RM(3, m) tree, LLRs `a`, at span offset OFF: its
+    // LLRs wait in the lane's column of level S while its left child RM(2, S-1) runs; paths
+    // created meanwhile inherit the lane whose column holds their ancestor's LLRs
+    template <int S, int OFF>
+    __device__ __forceinline__ static void node3(const Ctx& c, Path& p, float (&a)[1 << S]) {
+        if constexpr (S == 4) {
+            spc_leaf<OFF, 16>(c, p, a);
+        } else {
+            constexpr int HS = 1 << (S - 1);
+            constexpr int LV = S == M - 1 ? 0 : 1;
+            static_assert(S == M - 1 || (S == M - 2 && COL1 > 0), "a column per pending level");
+            float* colbase = c.pend + (LV == 0 ? 0 : H * 32);
+            const int lane = c.dbase + c.l;
+            __syncwarp();
+#pragma unroll
+            for (int e = 0; e < 2 * HS; e++) colbase[32 * e + lane] = a[e];
+            __syncwarp();
+            p.own[LV] = lane;
+            float ch[HS];
+#pragma unroll
+            for (int e = 0; e < HS; e++) ch[e] = fminsum(a[e], a[e + HS]);
+            node2<S - 1, OFF, false>(c, p, ch);
+            const float* pa = colbase + p.own[LV];
+#pragma unroll
+            for (int e = 0; e < HS; e++) ch[e] = g_fn(pa[32 * e], pa[32 * (e + HS)], bit(p, OFF + e));
+            node3<S - 1, OFF + HS>(c, p, ch);
             combine<OFF, HS>(p);
         }
     }
@@ -509,6 +663,12 @@ struct Ppt {
             if constexpr (G == 2) acc[0] += __shfl_xor_sync(kFull, acc[0], 1);
             lm[q] = acc[0];
         }
+        return pick_by_rank(c, lm);
+    }
+
+    // The candidate of rank l among the decoder's 2L by (LM descending, c ascending), where
+    // lane l of the path holds LM of candidates l and l + L.
+    __device__ __forceinline__ static int pick_by_rank(const Ctx& c, const float (&lm)[2]) {
         if constexpr (L == 1) {
             return (lm[1] > lm[0]) ? 1 : 0;
         } else {
@@ -541,6 +701,8 @@ struct Ppt {
     __device__ __forceinline__ static void run(const Ctx& c, Path& p) {
         p.rootc = select_root(c);
         p.pm = (c.single && (p.rootc & (L - 1)) != 0) ? __int_as_float(0x7f800000) : 0.f;
+        p.selc = 0;
+        p.own[0] = p.own[1] = c.dbase + G * c.l + c.g;
 #pragma unroll
         for (int w = 0; w < NW; w++) p.x[w] = 0;
         constexpr int VH = H / G;  // this lane's positions of a root child: G e + g
@@ -555,7 +717,7 @@ struct Ppt {
             sa = r[M - 1];
             sb = r[10] ^ ((G == 2 && c.g) ? col[0] : 0);  // the image of position g
         };
-        // f: left child RM(1, m-1) from y through the path's root permutation, this lane's
+        // f: left child RM(r-1, m-1) from y through the path's root permutation, this lane's
         // positions in Gray-code order of e (one XOR per position)
         load_rec();
         {
@@ -567,9 +729,13 @@ struct Ppt {
                 a[e] = fminsum(c.y[s], c.y[s ^ sa]);
             }
         }
-        float none[1];
-        fht_leaf<M - 1, 0, 0>(c, p, a, none);
-        // g: right child RM(2, m-1) from y through the (possibly new) path's permutation
+        if constexpr (R == 2) {
+            float none[1];
+            fht_leaf<M - 1, 0, 0>(c, p, a, none);
+        } else {
+            node2p<M - 1>(c, p, a);
+        }
+        // g: right child RM(r, m-1) from y through the (possibly new) path's permutation
         load_rec();
         {
             int s = sb;
@@ -580,7 +746,8 @@ struct Ppt {
                 a[e] = g_fn(c.y[s], c.y[s ^ sa], bitg(p, G * e, c.g));
             }
         }
-        node2<M - 1, H>(c, p, a);
+        if constexpr (R == 2) node2<M - 1, H>(c, p, a);
+        else node3<M - 1, H>(c, p, a);
     }
 };
 
@@ -590,15 +757,15 @@ struct Ppt {
 constexpr int kPptSlotWords = 128;
 
 // Resident CTAs of 4 warps the register budget is sized for: 168 registers per thread for
-// m >= 6 (measured on RM(2,7) P=8 L=4: 79.0 M frames/s, against 71.0 M at 128 registers, where
-// the largest leaf spills), 102 for shorter codes.
-__host__ __device__ constexpr int ppt_min_blocks(int m) { return m >= 6 ? 3 : 5; }
+// m >= 6 and for RM(3, m) (measured on RM(2,7) P=8 L=4: 79.0 M frames/s, against 71.0 M at 128
+// registers, where the largest leaf spills), 102 for shorter RM(2, m) codes.
+__host__ __device__ constexpr int ppt_min_blocks(int m, int r) { return (m >= 6 || r == 3) ? 3 : 5; }
 
-template <int M, int L>
-__global__ void __launch_bounds__(128, ppt_min_blocks(M)) ppt_kernel(LaunchArgs a) {
-    using D = Ppt<M, L>;
+template <int M, int R, int L>
+__global__ void __launch_bounds__(128, ppt_min_blocks(M, R)) ppt_kernel(LaunchArgs a) {
+    using D = Ppt<M, R, L>;
     constexpr int N = D::N, NW = D::NW, NREC = D::NREC, DL = D::DL;
-    constexpr int K = 1 + M + M * (M - 1) / 2;  // information bits of RM(2, m)
+    constexpr int K = 1 + M + M * (M - 1) / 2 + (R == 3 ? M * (M - 1) * (M - 2) / 6 : 0);  // of RM(r, m)
     constexpr int KW = (K + 31) / 32;
     extern __shared__ __align__(16) uint8_t smem[];
     const int FW = ppt_frame_lanes(M, L, a.P);
@@ -694,6 +861,7 @@ __global__ void __launch_bounds__(128, ppt_min_blocks(M)) ppt_kernel(LaunchArgs 
             const bool dvalid = d < a.P;
             const int dd = dvalid ? d : a.P - 1;
             c.rec = s_rec + dd * 2 * NREC * kRec;
+            c.rinv = c.rec + NREC * kRec;
             typename D::Path p;
             D::run(c, p);
             // Algorithm 5 over the batch: the smallest metric (NaN last), earlier decoders

@@ -667,7 +667,7 @@ rmdec_status rmdec_set_kernel(rmdec_t h, rmdec_kernel kernel) {
     rmdec_host::KernelEntry e;
     if (kernel == RMDEC_KERNEL_PATH &&
         (h->algo != 0 || h->hadamard != RMDEC_HADAMARD_SHUFFLE || !rmdec_host::lookup_pfht_ppt(h->m, h->r, h->L, h->P, &e)))
-        return h->fail(RMDEC_EINVAL, "no path-per-thread kernel for this decoder (RM(2, m), 4 <= m <= 8, L <= 8)");
+        return h->fail(RMDEC_EINVAL, "no path-per-thread kernel for this decoder (RM(2, m), 4 <= m <= 8, or RM(3, m), 5 <= m <= 7; L <= 8)");
     if (kernel != h->kernel) {
         h->kernel = kernel;
         h->dirty = true;  // the next decode looks up the kernel again

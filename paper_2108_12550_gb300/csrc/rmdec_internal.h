@@ -46,9 +46,11 @@ bool lookup_pfht_l32_small(int m, int r, KernelEntry* e);  // m = 4 .. 7
 bool lookup_pfht_l32_m8(int r, KernelEntry* e);
 bool lookup_pfht_l32_m9(int r, KernelEntry* e);
 
-// Path-per-thread kernels for RM(2, m), 4 <= m <= 8, L in {1, 2, 4, 8} (inst_ppt.cu); the
-// entry's shared-memory sizes depend on the decoder count P.
+// Path-per-thread kernels for RM(2, m), 4 <= m <= 8, and RM(3, m), 5 <= m <= 7, with L in
+// {1, 2, 4, 8} (inst_ppt.cu, inst_ppt3.cu); the entry's shared-memory sizes depend on the
+// decoder count P.
 bool lookup_pfht_ppt(int m, int r, int L, int P, KernelEntry* e);
+bool lookup_pfht_ppt3(int m, int L, int P, KernelEntry* e);
 
 // p-FHT-FSCL kernels whose FHTL nodes use the tensor cores (inst_tc.cu).
 bool lookup_pfht_tc(int m, int r, int L, KernelEntry* e);

@@ -140,7 +140,7 @@ def test_kernel_choice_is_checked_on_the_host():
     d.set_kernel("path")
     d.set_kernel("warp")
     d.set_kernel("auto")
-    for bad in [pkg.Decoder(9, 2, 4, 4), pkg.Decoder(6, 3, 4, 4), pkg.Decoder(6, 2, 4, 16),
+    for bad in [pkg.Decoder(9, 2, 4, 4), pkg.Decoder(8, 3, 4, 4), pkg.Decoder(6, 2, 4, 16),
                 pkg.Decoder(7, 2, 8, algo="autssc"), pkg.Decoder(7, 1, 2, 4)]:
         with pytest.raises(pkg.RmdecError) as ei:
             bad.set_kernel("path")
@@ -148,3 +148,4 @@ def test_kernel_choice_is_checked_on_the_host():
     assert d._lib.rmdec_set_kernel(d._h, 7) == pkg.EINVAL
     pkg.Decoder(4, 2, 128, 8).set_kernel("path")
     pkg.Decoder(8, 2, 20, 8).set_kernel("path")
+    pkg.Decoder(7, 3, 20, 8).set_kernel("path")

@@ -1,5 +1,5 @@
 """The path-per-thread kernel (one thread per list path, two for m = 8; RM(2, m) with
-4 <= m <= 8, L <= 8)
+4 <= m <= 8 and RM(3, m) with 5 <= m <= 7, L <= 8)
 against the warp-per-decoder kernel and the oracle, through the C ABI.
 
 Both kernels run the same method (Algorithms 2-5), so on integer LLRs (INT8, INT16, FP32
@@ -35,13 +35,12 @@ def _both(m, r, P, L, x, dtype, perms):
 
 # (m, P, L, frames): every list size, batches of decoders (P * L > 32), idle decoder slots
 # (P * L not a power of two) and ragged frame counts (not a multiple of the frames per warp)
-CASES = [(m, P, L, nf) for m in (4, 5, 6, 7, 8) for (P, L, nf) in
-         [(1, 1, 333), (3, 2, 250), (8, 4, 200), (20, 4, 61), (2, 8, 97), (5, 8, 33)]]
+CASES = [(m, r, P, L, nf) for (m, r) in [(4, 2), (5, 2), (6, 2), (7, 2), (8, 2), (5, 3), (6, 3), (7, 3)]
+         for (P, L, nf) in [(1, 1, 333), (3, 2, 250), (8, 4, 200), (20, 4, 61), (2, 8, 97), (5, 8, 33)]]
 
 
-@pytest.mark.parametrize("m,P,L,nf", CASES, ids=lambda v: str(v))
-def test_integer_llrs_identical_to_the_warp_kernel(m, P, L, nf):
-    r = 2
+@pytest.mark.parametrize("m,r,P,L,nf", CASES, ids=lambda v: str(v))
+def test_integer_llrs_identical_to_the_warp_kernel(m, r, P, L, nf):
     fr = I.make_frames(m, r, nf, 1.5 + 0.25 * L, seed=500 + 10 * m + L)
     q = I.quantize_i8(fr["llr"])
     perms = I.perm_table(m, r, P, L, seed=m + 3 * L + P)
@@ -50,9 +49,9 @@ def test_integer_llrs_identical_to_the_warp_kernel(m, P, L, nf):
         assert np.array_equal(a, b), name
 
 
-@pytest.mark.parametrize("m,P,L", [(5, 4, 2), (7, 8, 4), (6, 3, 8), (4, 2, 1), (8, 8, 4), (8, 3, 8), (8, 2, 1)])
-def test_integer_llrs_match_the_oracle(m, P, L):
-    r = 2
+@pytest.mark.parametrize("m,r,P,L", [(5, 2, 4, 2), (7, 2, 8, 4), (6, 2, 3, 8), (4, 2, 2, 1), (8, 2, 8, 4),
+                                     (8, 2, 3, 8), (8, 2, 2, 1), (5, 3, 3, 4), (6, 3, 2, 8), (7, 3, 8, 4), (7, 3, 1, 1)])
+def test_integer_llrs_match_the_oracle(m, r, P, L):
     fr = I.make_frames(m, r, 300, 2.0, seed=70 + m)
     q = I.quantize_i8(fr["llr"])
     perms = I.perm_table(m, r, P, L, seed=9 * m + L)
@@ -66,9 +65,8 @@ def test_integer_llrs_match_the_oracle(m, P, L):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f16", "i16"])
-@pytest.mark.parametrize("m,P,L", [(5, 4, 2), (7, 8, 4), (6, 20, 8), (8, 20, 4)])
-def test_other_input_types_agree_with_the_warp_kernel(m, P, L, dtype):
-    r = 2
+@pytest.mark.parametrize("m,r,P,L", [(5, 2, 4, 2), (7, 2, 8, 4), (6, 2, 20, 8), (8, 2, 20, 4), (7, 3, 8, 4)])
+def test_other_input_types_agree_with_the_warp_kernel(m, r, P, L, dtype):
     fr = I.make_frames(m, r, 1500, 2.5, seed=90 + m + L)
     if dtype == "f32":
         x = fr["llr"].astype(np.float32)
@@ -152,7 +150,8 @@ def test_kernel_choice_is_validated():
         pkg.Decoder(9, 2, 4, 4).set_kernel("path")  # no path-per-thread kernel for m = 9
     pkg.Decoder(8, 2, 20, 8).set_kernel("path")
     with pytest.raises(pkg.RmdecError):
-        pkg.Decoder(6, 3, 4, 4).set_kernel("path")  # nor for r = 3
+        pkg.Decoder(8, 3, 4, 4).set_kernel("path")  # nor for RM(3, 8)
+    pkg.Decoder(6, 3, 4, 4).set_kernel("path")
     with pytest.raises(pkg.RmdecError):
         pkg.Decoder(6, 2, 4, 16).set_kernel("path")  # nor for L = 16
     pkg.Decoder(7, 2, 20, 8).set_kernel("path")
