@@ -267,15 +267,17 @@ def test_p100_l1_bit_exact():
     assert np.array_equal(cw, ref["cw"]) and np.array_equal(best, ref["best"])
 
 
-@pytest.mark.parametrize("algo", ["pfht", "autssc"])
-def test_non_finite_llrs_give_in_range_results_and_leave_other_frames_alone(algo):
+@pytest.mark.parametrize("algo,kernel", [("pfht", "warp"), ("pfht", "path"), ("autssc", None)])
+def test_non_finite_llrs_give_in_range_results_and_leave_other_frames_alone(algo, kernel):
     """Frames holding NaN or infinite LLRs have no meaningful decision, but they must still
     return one of the decoders' codewords with an in-range winner index, and the other frames
-    of the batch must decode exactly as without them."""
+    of the batch must decode exactly as without them (both p-FHT-FSCL kernels)."""
     m, r, P, L = 7, 2, 8, 4
     fr = I.make_frames(m, r, 64, 2.0, seed=71)
     x = fr["llr"].astype(np.float32)
     dec = pkg.Decoder(m, r, P, L, perm_seed=3, algo=algo)
+    if kernel is not None:
+        dec.set_kernel(kernel)
     ref_info, ref_cw, ref_pm, ref_best = _gpu_decode(dec, x)
     bad = x.copy()
     bad[5, :] = np.nan
