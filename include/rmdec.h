@@ -113,8 +113,13 @@ rmdec_status rmdec_set_hadamard(rmdec_t h, rmdec_hadamard mode);
 
 /* Which kernel runs a p-FHT-FSCL decode (Algorithms 2-5; the same method either way).
  * AUTO (default): WARP, and PATH for launches of at least 512 (RM(2, m <= 5)), 2,048 (RM(2, 6),
- *   RM(2, 7), RM(3, m)) or 8,192 (RM(2, 8)) frames where it exists (measured crossovers: the
- *   warp kernel answers small launches sooner, the path kernel has the higher throughput).
+ *   RM(2, 7), RM(3, m)) or 8,192 (RM(2, 8)) frames where it exists and was measured faster for
+ *   the decoder's P and L (the warp kernel answers small launches sooner, the path kernel has
+ *   the higher throughput unless the decoders' tables leave it few CTAs per SM or its L = 8
+ *   candidate lists cost more). PATH by default for P in: RM(2, m <= 6) 1..128 (L = 8: 1..32);
+ *   RM(3, 5) and RM(3, 6) 1..128 (L = 4: 1..64; L = 8: 1..20 and 1..16); RM(2, 7) 4..128
+ *   (L = 4: 4..64; L = 8: 4..8); RM(3, 7) 4..128 (L = 4: 1..32; L = 8: 4); RM(2, 8) 4..128
+ *   (L = 4: 4..20; L = 8: never). rmdec_kernel_for reports the choice for a launch size.
  * WARP: one warp per decoder, the L paths spread over its lanes and the tree's LLR buffers in
  *   shared memory; every supported code.
  * PATH: one thread per list path (two for m = 8), the tree's LLRs in registers, the decoders
@@ -130,6 +135,11 @@ typedef enum {
     RMDEC_KERNEL_PATH = 2,
 } rmdec_kernel;
 rmdec_status rmdec_set_kernel(rmdec_t h, rmdec_kernel kernel);
+/* The kernel that decodes a launch of n_frames frames with the handle's current settings:
+ * RMDEC_KERNEL_PATH or RMDEC_KERNEL_WARP (also reported for Aut-SSC handles and for RM(1, m) and
+ * RM(m-1, m) roots, whose kernels have no path-per-thread form). Uploads the handle's tables to
+ * the current device if needed (as a decode would). Not part of the paper's method. */
+rmdec_status rmdec_kernel_for(rmdec_t h, int64_t n_frames, rmdec_kernel *kernel);
 
 /* Number of uint16 permutation records the handle holds (11 uint16 per record:
  * [c_0 .. c_9, b] with c_t = A e_t; the record maps index i to b XOR sum_{t: i_t = 1} c_t).

@@ -53,6 +53,7 @@ def load_library():
         "rmdec_set_dtype": ([V, I], I),
         "rmdec_set_hadamard": ([V, I], I),
         "rmdec_set_kernel": ([V, I], I),
+        "rmdec_kernel_for": ([V, I64, ctypes.POINTER(I)], I),
         "rmdec_perm_count": ([V, ctypes.POINTER(I64)], I),
         "rmdec_get_perms": ([V, V, I64], I),
         "rmdec_set_perms": ([V, V, I64], I),
@@ -160,6 +161,12 @@ class Decoder:
         RM(3, m) with 5 <= m <= 7, and L <= 8)."""
         self._check(self._lib.rmdec_set_kernel(self._h, {"auto": 0, "warp": 1, "path": 2}[kernel]))
         self.kernel = kernel
+
+    def kernel_for(self, n_frames):
+        """'path' or 'warp': the kernel that decodes a launch of n_frames frames now."""
+        k = ctypes.c_int()
+        self._check(self._lib.rmdec_kernel_for(self._h, ctypes.c_int64(n_frames), ctypes.byref(k)))
+        return {1: "warp", 2: "path"}[k.value]
 
     def perm_count(self):
         n = ctypes.c_int64()

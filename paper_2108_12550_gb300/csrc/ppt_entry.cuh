@@ -6,6 +6,25 @@
 
 namespace rmdec_host {
 
+// Decoders per frame P for which the default choice gives large launches to this kernel: the
+// P where it decoded 16,384 FP32 frames at least 10% faster than the warp-per-decoder kernel,
+// measured at P = 1, 4, 8, 16, 20, 32, 64 and 128 (P between two measured values counts as
+// outside unless both were inside). Outside, either the frame's lane group holds too few paths
+// (P = 1 for m >= 7: one path in 4 or 8 lanes), or the decoders' tables in shared memory leave
+// few CTAs per SM (large P), or the L = 8 candidate lists cost more than the warp kernel's
+// selection (RM(2,8), and RM(2,7) or RM(3,7) beyond P = 8 or 4).
+struct PptAutoRange {
+    int pmin, pmax;  // pmin > pmax: never
+};
+constexpr PptAutoRange ppt_auto_range(int M, int R, int L) {
+    if (R == 2 && M <= 6) return {1, L <= 4 ? 128 : 32};
+    if (R == 3 && M <= 6) return {1, L <= 2 ? 128 : (L == 4 ? 64 : (M == 5 ? 20 : 16))};
+    if (R == 2 && M == 7) return {4, L <= 2 ? 128 : (L == 4 ? 64 : 8)};
+    if (R == 3 && M == 7) return L <= 2 ? PptAutoRange{4, 128} : (L == 4 ? PptAutoRange{1, 32} : PptAutoRange{4, 4});
+    if (R == 2 && M == 8) return {4, L <= 2 ? 128 : (L == 4 ? 20 : 0)};
+    return {1, 0};
+}
+
 template <int M, int R, int L>
 bool ppt_entry(int P, KernelEntry* e) {
     using D = rmdec_dev::Ppt<M, R, L>;
@@ -27,6 +46,8 @@ bool ppt_entry(int P, KernelEntry* e) {
     // INT8 / P=20 from 2,048, RM(2,8) P=8 / P=20 from 8,192; RM(3,5) P=4 L=2, RM(3,6) P=8,
     // RM(3,7) P=8 / P=20 between 512 and 2,048.
     e->min_frames = R == 3 ? 2048 : (M <= 5 ? 512 : (M <= 7 ? 2048 : 8192));
+    constexpr PptAutoRange ar = ppt_auto_range(M, R, L);
+    e->auto_ok = P >= ar.pmin && P <= ar.pmax;
     return true;
 }
 

@@ -216,6 +216,7 @@ size_t llr_elem_bytes(rmdec_dtype t) {
 
 bool lookup_kernel(rmdec_ctx* h, rmdec_host::KernelEntry* e) {
     using namespace rmdec_host;
+    *e = KernelEntry();  // the per-kernel lookups fill only the fields their kind uses
     if (h->algo == 1) return lookup_autssc(h->m, h->r, e);
     if (h->algo == 2) return lookup_mlroot(h->m, h->r, e);
     if (h->hadamard == RMDEC_HADAMARD_TENSOR) return lookup_pfht_tc(h->m, h->r, h->L, e);
@@ -242,7 +243,9 @@ bool lookup_kernel(rmdec_ctx* h, rmdec_host::KernelEntry* e) {
 bool lookup_path_alternative(rmdec_ctx* h, rmdec_host::KernelEntry* e) {
     *e = rmdec_host::KernelEntry();
     if (h->algo != 0 || h->kernel != RMDEC_KERNEL_AUTO || h->hadamard != RMDEC_HADAMARD_SHUFFLE) return false;
-    return rmdec_host::lookup_pfht_ppt(h->m, h->r, h->L, h->P, e);
+    if (!rmdec_host::lookup_pfht_ppt(h->m, h->r, h->L, h->P, e)) return false;
+    if (!e->auto_ok) *e = rmdec_host::KernelEntry();  // slower for this P and L: not by default
+    return e->fn != nullptr;
 }
 
 // Device records: p-FHT-FSCL: per decoder, level 0 holds the 2L root candidates composed with
@@ -673,6 +676,17 @@ rmdec_status rmdec_set_kernel(rmdec_t h, rmdec_kernel kernel) {
         h->dirty = true;  // the next decode looks up the kernel again
         h->shape_dirty = true;
     }
+    return RMDEC_OK;
+}
+
+rmdec_status rmdec_kernel_for(rmdec_t h, int64_t n_frames, rmdec_kernel* kernel) {
+    if (!h || !kernel) return RMDEC_EINVAL;
+    if (n_frames < 0) return h->fail(RMDEC_EINVAL, "n_frames < 0");
+    rmdec_status st = ensure_device(h);
+    if (st == RMDEC_OK) st = configure_shape(h);
+    if (st != RMDEC_OK) return st;
+    const bool path = h->kern.frames_per_warp != 0 || (h->kern_path.fn && n_frames >= h->kern_path.min_frames);
+    *kernel = path ? RMDEC_KERNEL_PATH : RMDEC_KERNEL_WARP;
     return RMDEC_OK;
 }
 

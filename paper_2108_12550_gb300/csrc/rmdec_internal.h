@@ -28,6 +28,8 @@ struct KernelEntry {
     int frames_per_warp = 0;   // path-per-thread kernels: frames a CTA decodes at once (else 0)
     int batches = 0;           // path-per-thread kernels: decoder batches per frame
     int64_t min_frames = 0;    // path-per-thread kernels: smallest launch they take by default
+    bool auto_ok = true;       // path-per-thread kernels: faster than the warp-per-decoder
+                               // kernel for this P (the default choice may take it)
 };
 
 // p-FHT-FSCL kernels: one lookup per code length m (instantiated in inst_m<m>.cu).

@@ -28,6 +28,19 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, n), n
 
 
+def test_kernel_query_checks_its_arguments():
+    lib = pkg.load_library()
+    k = ctypes.c_int()
+    assert lib.rmdec_kernel_for(None, 10, ctypes.byref(k)) == pkg.EINVAL
+    h = ctypes.c_void_p()
+    assert lib.rmdec_create(ctypes.byref(h), 7, 2, 8, 4, 1) == pkg.OK
+    try:
+        assert lib.rmdec_kernel_for(h, 10, None) == pkg.EINVAL
+        assert lib.rmdec_kernel_for(h, -1, ctypes.byref(k)) == pkg.EINVAL
+    finally:
+        lib.rmdec_destroy(h)
+
+
 def test_invalid_configurations_are_rejected():
     lib = pkg.load_library()
     h = ctypes.c_void_p()

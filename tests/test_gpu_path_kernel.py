@@ -155,3 +155,23 @@ def test_kernel_choice_is_validated():
     with pytest.raises(pkg.RmdecError):
         pkg.Decoder(6, 2, 4, 16).set_kernel("path")  # nor for L = 16
     pkg.Decoder(7, 2, 20, 8).set_kernel("path")
+
+
+@pytest.mark.parametrize("m,r,P,L,path", [
+    (7, 2, 8, 4, True), (5, 2, 128, 4, True), (6, 3, 16, 8, True), (8, 2, 20, 4, True), (7, 3, 1, 4, True),
+    (6, 2, 32, 8, True), (7, 2, 1, 1, False), (8, 2, 8, 8, False), (5, 2, 64, 8, False), (6, 3, 20, 8, False),
+    (8, 2, 32, 4, False), (7, 3, 8, 8, False), (7, 2, 2, 4, False), (9, 2, 20, 4, False)])
+def test_auto_takes_the_path_kernel_only_where_it_was_measured_faster(m, r, P, L, path):
+    # large launches go to the path-per-thread kernel only for the P and L where it decoded
+    # faster than the warp kernel (large P leaves it few CTAs per SM; L = 8 costs it more)
+    dec = pkg.Decoder(m, r, P, L, perm_seed=1)
+    assert dec.kernel_for(1 << 16) == ("path" if path else "warp")
+    assert dec.kernel_for(64) == "warp"
+    if (m, r) != (9, 2):
+        fresh = pkg.Decoder(m, r, P, L, perm_seed=1)
+        fresh.set_kernel("warp")
+        dec.set_kernel("path")  # forced, it takes every launch
+        assert dec.kernel_for(1) == "path"
+        dec.set_kernel("warp")  # and back: the warp kernel in its own launch shape
+        assert dec.kernel_for(1 << 16) == "warp"
+        assert dec.get_tuning() == fresh.get_tuning()
