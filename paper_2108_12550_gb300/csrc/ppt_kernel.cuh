@@ -136,6 +136,7 @@ struct Ppt {
         int l;                  // this lane's path
         int g;                  // this lane within its path (positions G e + g)
         bool single;            // paths 1..L-1 start inactive (metric +inf)
+        bool int8;              // INT8 LLR codes (every tree value an integer, see fht_leaf)
     };
     struct Path {
         float pm;
@@ -267,32 +268,65 @@ struct Ppt {
         // (sentinel -1) and 2k + [c_k < 0]
         float tv[T];
         unsigned tk[T];
+        if (M >= 6 && c.int8) {
+            // (codes of length 32 and less keep the one list form: this one measured 1.5%
+            // slower there, its extra code outweighing the leaves' few values)
+            // INT8 codes: every |c_k| is an integer of at most 2^m x 128 <= 2^15 (each tree
+            // level at most doubles an LLR, a length-2^s transform at depth m - s multiplies it
+            // by at most 2^s), so its FP32 pattern has at least 8 zero low bits. They take
+            // (VS - 1 - e, [c_k < 0]), which turns (|c| descending, e ascending) into the
+            // descending order of one integer: the list update is a max/min network
+            constexpr int EB = cilog2(VS);
+            static_assert(M <= 8 && 1 + EB <= 8, "index and sign fit the zero low bits");
+            constexpr unsigned LOW = (2u << EB) - 1u;
+            unsigned pk[T];
 #pragma unroll
-        for (int j = 0; j < T; j++) {
-            tv[j] = -1.f;
-            tk[j] = 2u * (G * j + c.g);
-        }
+            for (int j = 0; j < T; j++) pk[j] = 0u;  // below every key (VS >= T keys follow)
 #pragma unroll
-        for (int e = 0; e < VS; e++) {
-            const float x = fabsf(v[e]);
-            const unsigned xk = 2u * (G * e + c.g) + (v[e] < 0.f ? 1u : 0u);
-            // the new list from the old one: entry j keeps, takes x, or takes entry j - 1
-            bool gt[T];
+            for (int e = 0; e < VS; e++) {
+                const unsigned b = __float_as_uint(v[e]);
+                const unsigned x = (b & 0x7fffffffu) | ((unsigned)(VS - 1 - e) << 1) | (b > 0x80000000u ? 1u : 0u);
+                unsigned np[T];
+                np[0] = umax(pk[0], x);
 #pragma unroll
-            for (int j = 0; j < T; j++) gt[j] = x > tv[j];
-            float ntv[T];
-            unsigned ntk[T];
-            ntv[0] = gt[0] ? x : tv[0];
-            ntk[0] = gt[0] ? xk : tk[0];
+                for (int j = 1; j < T; j++) np[j] = umax(pk[j], umin(pk[j - 1], x));
 #pragma unroll
-            for (int j = 1; j < T; j++) {
-                ntv[j] = gt[j - 1] ? tv[j - 1] : (gt[j] ? x : tv[j]);
-                ntk[j] = gt[j - 1] ? tk[j - 1] : (gt[j] ? xk : tk[j]);
+                for (int j = 0; j < T; j++) pk[j] = np[j];
             }
 #pragma unroll
             for (int j = 0; j < T; j++) {
-                tv[j] = ntv[j];
-                tk[j] = ntk[j];
+                tv[j] = __uint_as_float(pk[j] & ~LOW);
+                const unsigned e = (unsigned)(VS - 1) - ((pk[j] >> 1) & (unsigned)(VS - 1));
+                tk[j] = 2u * (G * e + (unsigned)c.g) + (pk[j] & 1u);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < T; j++) {
+                tv[j] = -1.f;
+                tk[j] = 2u * (G * j + c.g);
+            }
+#pragma unroll
+            for (int e = 0; e < VS; e++) {
+                const float x = fabsf(v[e]);
+                const unsigned xk = 2u * (G * e + c.g) + (v[e] < 0.f ? 1u : 0u);
+                // the new list from the old one: entry j keeps, takes x, or takes entry j - 1
+                bool gt[T];
+#pragma unroll
+                for (int j = 0; j < T; j++) gt[j] = x > tv[j];
+                float ntv[T];
+                unsigned ntk[T];
+                ntv[0] = gt[0] ? x : tv[0];
+                ntk[0] = gt[0] ? xk : tk[0];
+#pragma unroll
+                for (int j = 1; j < T; j++) {
+                    ntv[j] = gt[j - 1] ? tv[j - 1] : (gt[j] ? x : tv[j]);
+                    ntk[j] = gt[j - 1] ? tk[j - 1] : (gt[j] ? xk : tk[j]);
+                }
+#pragma unroll
+                for (int j = 0; j < T; j++) {
+                    tv[j] = ntv[j];
+                    tk[j] = ntk[j];
+                }
             }
         }
         // keys (PM', path 2^(S+1) + 2k + sign) of the lane's list, in ascending order
@@ -801,6 +835,7 @@ __global__ void __launch_bounds__(128, ppt_min_blocks(M, R)) ppt_kernel(LaunchAr
     c.l = (j % DL) / D::G;
     c.g = j % D::G;
     c.single = a.single_start != 0;
+    c.int8 = a.dtype == IN_I8;
     const unsigned gmask = FW == 32 ? 0xffffffffu : ((1u << FW) - 1u);
     const size_t eb = a.dtype == IN_F32 ? 4 : (a.dtype == IN_I8 ? 1 : 2);
     const int64_t nblk = (a.n_frames + FPW - 1) / FPW;
