@@ -37,19 +37,26 @@ WORKLOADS = {
     "rm28_p8_l4": (8, 2, 8, 4, 3.0, 1 << 19),  # a serving-mix code
 }
 METRIC = "frames/s RM(2,9) P=20 L=4 at FER~1e-4 Eb/N0; p50/p99 latency, mixed load"
-# DRAM bytes per frame of one ncu capture of pfht_kernel<9,2,4> (16,384 frames: 33,641,728 B
-# read + 0 B written), valid only for the kernel code it was taken on (the prefix of
-# kernel_fingerprint())
-TRAFFIC = {"rm29_p20_l4": {"bytes_per_frame": (33641728 + 0) / 16384, "kernel_code_sha256": "4e5d0ffbfdf3aa35"}}
+# DRAM bytes per frame of one ncu capture per (workload, LLR type), valid only for the kernel
+# that decodes the workload's launches and the code it was taken on (the prefix of
+# kernel_fingerprint() of that kernel's source): pfht_kernel<9,2,4> on 16,384 FP32 frames
+# (33,641,728 B read + 0 B written), ppt_kernel<7,2,4> on 65,536 INT8 frames (8,531,200 B read
+# + 0 B written)
+TRAFFIC = {
+    ("rm29_p20_l4", "f32"): {"kernel": "warp", "source": "pfht_kernel.cuh",
+                             "bytes_per_frame": (33641728 + 0) / 16384, "kernel_code_sha256": "4e5d0ffbfdf3aa35"},
+    ("rm27_p8_l4", "i8"): {"kernel": "path", "source": "ppt_kernel.cuh",
+                           "bytes_per_frame": (8531200 + 0) / 65536, "kernel_code_sha256": "91ef0b69b44bb38c"},
+}
 LANES_PER_SM = 128  # INT32/FP32 lanes per SM: one ALU operation per lane per clock
 
 
-def kernel_fingerprint():
-    """sha256 of the kernel source with comments and blank lines removed: a capture stays
+def kernel_fingerprint(source="pfht_kernel.cuh"):
+    """sha256 of a kernel source with comments and blank lines removed: a capture stays
     valid across comment edits and goes stale on any code change."""
     import hashlib
 
-    with open(os.path.join(ROOT, "paper_2108_12550_gb300", "csrc", "pfht_kernel.cuh")) as fh:
+    with open(os.path.join(ROOT, "paper_2108_12550_gb300", "csrc", source)) as fh:
         code = re.sub(r"//[^\n]*", "", fh.read())
     code = "\n".join(line.strip() for line in code.splitlines() if line.strip())
     return hashlib.sha256(code.encode()).hexdigest()
@@ -619,8 +626,9 @@ def main():
     else:
         bound, achieved, peak, unit = "hbm", bytes_frame * nf / t_launch / 1e9, hbm_bw / 1e9, "GB/s"
     traffic = None
-    tr = TRAFFIC.get(args.workload)
-    if tr and args.dtype == "f32" and kernel_fingerprint().startswith(tr["kernel_code_sha256"]):
+    tr = TRAFFIC.get((args.workload, args.dtype))
+    if (tr and args.hadamard == "shuffle" and dec.kernel_for(nf) == tr["kernel"]
+            and kernel_fingerprint(tr["source"]).startswith(tr["kernel_code_sha256"])):
         traffic = tr["bytes_per_frame"] * nf  # scaled from the captured case by frames
     line = {
         "metric": METRIC if args.workload == "rm29_p20_l4" else f"frames/s {args.workload}",
