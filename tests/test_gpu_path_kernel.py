@@ -175,3 +175,25 @@ def test_auto_takes_the_path_kernel_only_where_it_was_measured_faster(m, r, P, L
         dec.set_kernel("warp")  # and back: the warp kernel in its own launch shape
         assert dec.kernel_for(1 << 16) == "warp"
         assert dec.get_tuning() == fresh.get_tuning()
+
+
+@pytest.mark.parametrize("m,r,P,L", [(8, 2, 8, 4), (8, 2, 3, 8), (7, 2, 8, 4), (6, 2, 4, 2), (7, 3, 4, 4), (6, 3, 2, 8)])
+def test_full_range_int8_codes_match_the_oracle(m, r, P, L):
+    # INT8 codes over their whole range, -128 included (the quantiser stops at -127): frames
+    # all -128 or all 127 reach the largest spectrum values, 2^m x 128, where the kernel's
+    # packed candidate keys have the fewest spare bits; all-zero frames tie everything
+    n = 1 << m
+    rng = np.random.default_rng(1000 + 10 * m + L)
+    q = rng.integers(-128, 128, size=(96, n)).astype(np.int8)
+    q[0], q[1], q[3] = -128, 127, 0
+    q[2] = np.where(np.arange(n) % 3 == 0, -128, 127)
+    fr = I.make_frames(m, r, 40, 2.0, seed=20 + m)
+    q[4:44] = np.clip(np.rint(fr["llr"] * 16), -128, 127).astype(np.int8)  # saturated channel frames
+    perms = I.perm_table(m, r, P, L, seed=7 * m + L)
+    ref = O.decode(m, r, P, L, perms, q.astype(np.int64), integer=True)
+    dec = pkg.Decoder(m, r, P, L, dtype="i8", perms=perms)
+    dec.set_kernel("path")
+    bits, cw, pm, best = _run(dec, q)
+    assert np.array_equal(pkg.unpack_bits(cw, dec.n), ref["cw"])
+    assert np.array_equal(pm.astype(np.int64), ref["pm"]) and np.array_equal(best, ref["best"])
+    assert np.array_equal(pkg.unpack_bits(bits, dec.k), ref["info"])
