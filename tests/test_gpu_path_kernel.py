@@ -177,11 +177,15 @@ def test_auto_takes_the_path_kernel_only_where_it_was_measured_faster(m, r, P, L
         assert dec.get_tuning() == fresh.get_tuning()
 
 
-@pytest.mark.parametrize("m,r,P,L", [(8, 2, 8, 4), (8, 2, 3, 8), (7, 2, 8, 4), (6, 2, 4, 2), (7, 3, 4, 4), (6, 3, 2, 8)])
-def test_full_range_int8_codes_match_the_oracle(m, r, P, L):
+@pytest.mark.parametrize("kernel", ["path", "warp"])
+@pytest.mark.parametrize("m,r,P,L", [(8, 2, 8, 4), (8, 2, 3, 8), (7, 2, 8, 4), (6, 2, 4, 2), (7, 3, 4, 4), (6, 3, 2, 8),
+                                     (9, 2, 20, 4), (9, 3, 4, 8)])
+def test_full_range_int8_codes_match_the_oracle(m, r, P, L, kernel):
     # INT8 codes over their whole range, -128 included (the quantiser stops at -127): frames
-    # all -128 or all 127 reach the largest spectrum values, 2^m x 128, where the kernel's
+    # all -128 or all 127 reach the largest spectrum values, 2^m x 128, where the path kernel's
     # packed candidate keys have the fewest spare bits; all-zero frames tie everything
+    if kernel == "path" and m == 9:
+        pytest.skip("no path-per-thread kernel for length 512")
     n = 1 << m
     rng = np.random.default_rng(1000 + 10 * m + L)
     q = rng.integers(-128, 128, size=(96, n)).astype(np.int8)
@@ -192,7 +196,7 @@ def test_full_range_int8_codes_match_the_oracle(m, r, P, L):
     perms = I.perm_table(m, r, P, L, seed=7 * m + L)
     ref = O.decode(m, r, P, L, perms, q.astype(np.int64), integer=True)
     dec = pkg.Decoder(m, r, P, L, dtype="i8", perms=perms)
-    dec.set_kernel("path")
+    dec.set_kernel(kernel)
     bits, cw, pm, best = _run(dec, q)
     assert np.array_equal(pkg.unpack_bits(cw, dec.n), ref["cw"])
     assert np.array_equal(pm.astype(np.int64), ref["pm"]) and np.array_equal(best, ref["best"])
